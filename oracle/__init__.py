@@ -1,0 +1,184 @@
+"""CPU oracle of the LDU pressure-solve path (test infrastructure only).
+
+A plain, sequential FP64 C implementation (``oracle.c``) loaded with ctypes,
+plus numpy glue.  Only the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import this package; the CUDA library shares
+no code with it.  See the header of ``oracle.c`` for each function's
+definition and the paper passage it follows.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+PRECOND_NONE, PRECOND_DIAGONAL, PRECOND_DIC = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            _declare(_lib)
+    return _lib
+
+
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_i8p = np.ctypeslib.ndpointer(np.int8, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+_i32 = C.c_int32
+_f64 = C.c_double
+
+
+def _declare(L):
+    L.oracle_assemble_laplacian.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _i32,
+                                            _i32p, _f64p, _f64p, _f64p, _i8p, _f64p, _f64p]
+    L.oracle_assemble_laplacian.restype = None
+    L.oracle_amul.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
+    L.oracle_amul.restype = None
+    L.oracle_amul_f32.argtypes = [_i32, _i32, _i32p, _i32p, _f32p, _f32p, _f32p, _f32p]
+    L.oracle_amul_f32.restype = None
+    L.oracle_dic_factor.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p]
+    L.oracle_dic_factor.restype = _i32
+    L.oracle_dic_precondition.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
+    L.oracle_dic_precondition.restype = None
+    L.oracle_dic_precondition_f32.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f32p, _f32p]
+    L.oracle_dic_precondition_f32.restype = None
+    L.oracle_diag_reciprocal.argtypes = [_i32, _f64p, _f64p]
+    L.oracle_diag_reciprocal.restype = None
+    L.oracle_norm_factor.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p]
+    L.oracle_norm_factor.restype = _f64
+    L.oracle_pcg.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _i32, _f64, _f64,
+                             _i32, _i32, _f64p]
+    L.oracle_pcg.restype = _i32
+    L.oracle_mixed_ir.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _i32, _f64,
+                                  _f64, _i32, _i32, _f64p]
+    L.oracle_mixed_ir.restype = _i32
+    L.oracle_adjoint.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _i32, _f64,
+                                 _i32, _f64p, _f64p, _f64p, _f64p]
+    L.oracle_adjoint.restype = _i32
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def assemble_laplacian(mesh, gamma, bgamma, btype):
+    """(upper[F], diag[N]) of A = -laplacian(gamma, p), Gauss linear corrected."""
+    upper = np.empty(mesh.n_faces)
+    diag = np.empty(mesh.n_cells)
+    lib().oracle_assemble_laplacian(mesh.n_cells, mesh.n_faces, _c(mesh.lower, np.int32),
+                                    _c(mesh.upper_addr, np.int32), _c(mesh.sf, np.float64),
+                                    _c(mesh.c, np.float64), _c(gamma, np.float64), mesh.n_bfaces,
+                                    _c(mesh.bface_cell, np.int32), _c(mesh.bface_sf, np.float64),
+                                    _c(mesh.bface_cf, np.float64), _c(bgamma, np.float64),
+                                    _c(btype, np.int8), upper, diag)
+    return upper, diag
+
+
+def amul(l, u, diag, upper, x):
+    n = len(diag)
+    if np.asarray(x).dtype == np.float32:
+        y = np.empty(n, dtype=np.float32)
+        lib().oracle_amul_f32(n, len(l), _c(l, np.int32), _c(u, np.int32), _c(diag, np.float32),
+                              _c(upper, np.float32), _c(x, np.float32), y)
+        return y
+    y = np.empty(n)
+    lib().oracle_amul(n, len(l), _c(l, np.int32), _c(u, np.int32), _c(diag, np.float64),
+                      _c(upper, np.float64), _c(x, np.float64), y)
+    return y
+
+
+def dic_factor(l, u, diag, upper):
+    """Returns (rD, first_bad_cell or -1)."""
+    rD = np.empty(len(diag))
+    bad = lib().oracle_dic_factor(len(diag), len(l), _c(l, np.int32), _c(u, np.int32),
+                                  _c(diag, np.float64), _c(upper, np.float64), rD)
+    return rD, int(bad)
+
+
+def dic_precondition(l, u, upper, rD, r):
+    n = len(rD)
+    if np.asarray(r).dtype == np.float32:
+        w = np.empty(n, dtype=np.float32)
+        lib().oracle_dic_precondition_f32(n, len(l), _c(l, np.int32), _c(u, np.int32),
+                                          _c(upper, np.float64), _c(rD, np.float64),
+                                          _c(r, np.float32), w)
+        return w
+    w = np.empty(n)
+    lib().oracle_dic_precondition(n, len(l), _c(l, np.int32), _c(u, np.int32), _c(upper, np.float64),
+                                  _c(rD, np.float64), _c(r, np.float64), w)
+    return w
+
+
+def diag_reciprocal(diag):
+    rD = np.empty(len(diag))
+    lib().oracle_diag_reciprocal(len(diag), _c(diag, np.float64), rD)
+    return rD
+
+
+def norm_factor(l, u, diag, upper, x, b):
+    q = amul(l, u, diag, upper, x)
+    return lib().oracle_norm_factor(len(diag), len(l), _c(l, np.int32), _c(u, np.int32),
+                                    _c(diag, np.float64), _c(upper, np.float64), _c(x, np.float64),
+                                    _c(b, np.float64), q)
+
+
+def pcg(l, u, diag, upper, b, x0=None, precond=PRECOND_DIC, tol=1e-8, rel_tol=0.0,
+        max_iter=20000, min_iter=0):
+    """Returns (x, perf dict)."""
+    n = len(diag)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    perf = np.zeros(5)
+    st = lib().oracle_pcg(n, len(l), _c(l, np.int32), _c(u, np.int32), _c(diag, np.float64),
+                          _c(upper, np.float64), _c(b, np.float64), x, int(precond), float(tol),
+                          float(rel_tol), int(max_iter), int(min_iter), perf)
+    return x, dict(status=int(st), initial_residual=perf[0], final_residual=perf[1],
+                   n_iter=int(perf[2]), singular=int(perf[3]), converged=int(perf[4]))
+
+
+def mixed_ir(l, u, diag, upper, b, x0=None, precond=PRECOND_DIC, tol=1e-8, inner_rel_tol=1e-4,
+             max_iter=20000, max_outer=20):
+    n = len(diag)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    perf = np.zeros(6)
+    st = lib().oracle_mixed_ir(n, len(l), _c(l, np.int32), _c(u, np.int32), _c(diag, np.float64),
+                               _c(upper, np.float64), _c(b, np.float64), x, int(precond), float(tol),
+                               float(inner_rel_tol), int(max_iter), int(max_outer), perf)
+    return x, dict(status=int(st), initial_residual=perf[0], final_residual=perf[1],
+                   n_iter=int(perf[2]), singular=int(perf[3]), converged=int(perf[4]),
+                   n_outer=int(perf[5]))
+
+
+def adjoint(l, u, diag, upper, x, g, precond=PRECOND_DIC, tol=1e-13, max_iter=20000):
+    """Returns (lambda, dL/dupper, dL/ddiag, perf)."""
+    n, nf = len(diag), len(l)
+    lam = np.empty(n)
+    du = np.empty(nf)
+    dd = np.empty(n)
+    perf = np.zeros(5)
+    st = lib().oracle_adjoint(n, nf, _c(l, np.int32), _c(u, np.int32), _c(diag, np.float64),
+                              _c(upper, np.float64), _c(x, np.float64), _c(g, np.float64),
+                              int(precond), float(tol), int(max_iter), lam, du, dd, perf)
+    return lam, du, dd, dict(status=int(st), n_iter=int(perf[2]), final_residual=perf[1])
