@@ -1,0 +1,385 @@
+#!/usr/bin/env python
+"""Benchmark of the LDU pressure solve on one GB300 (replicas on N GPUs).
+
+Workload (the 8M-cell configuration the metric is quoted on): a 200^3 hex
+block, interior points jittered by U(-0.2, 0.2) h, cells randomly permuted,
+faces re-sorted to upper-triangular order, face diffusivity log-normal
+(sigma = 1), Dirichlet p = 0 on x-max, b ~ N(0, 1), seed 3; DIC
+preconditioning, tolerance 1e-8 (normalised residual).
+
+One step = laplacian assembly from the resident geometry + the mixed-precision
+solve (FP32 DIC-PCG inside FP64 refinement) to 1e-8.  The FP64 solve of the
+same system and the stand-alone Amul are timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG time to 1e-8 rel. residual @8M cells (FP64 vs mixed); Amul HBM GB/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+# Iteration counts of this seeded workload (mixed: inner iterations, outer
+# steps), used only to project the CPU oracle's bounded sample to a full solve.
+PROJECTION_ITERS = {"inner": 1000, "outer": 3}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=200, help="mesh side (default 200: 8.0M cells)")
+    ap.add_argument("--cpu-iters", type=int, default=8, help="oracle inner iterations in the CPU sample")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max over ranks (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def workload_bytes(n_cells: int, n_faces: int):
+    """Algorithmic bytes (LDU basis, int32 indices) of one PCG iteration and of
+    one Amul: FP64 iteration 152N + 48F, FP32 iteration 76N + 36F, FP64 Amul
+    16F + 24N, FP32 Amul 12F + 12N, FP64 residual b - A x 16F + 40N."""
+    N, F = n_cells, n_faces
+    return dict(it64=152 * N + 48 * F, it32=76 * N + 36 * F, amul64=16 * F + 24 * N, amul32=12 * F + 12 * N,
+                resid64=16 * F + 40 * N)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                mx.append(float(parts[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_case(n: int):
+    import hexmesh
+    return hexmesh.pressure_case(n, jitter=0.2, permute=True, seed=3, lognormal_gamma=True)
+
+
+def cpu_sample(case, n_inner_sample: int):
+    """The oracle as it stands on the host cores: assembly, DIC factor, one FP64
+    residual and `n_inner_sample` FP32 inner iterations of the refinement,
+    projected to the workload's iteration counts.  Returns (ms per step, info)."""
+    import numpy as np
+    import oracle
+    m = case.mesh
+    t0 = time.perf_counter()
+    up, dg = oracle.assemble_laplacian(m, case.gamma, case.bgamma, case.btype)
+    t_asm = time.perf_counter() - t0
+    # mixed_ir with one outer step runs: factor, 2 FP64 residuals and k inner iterations
+    t0 = time.perf_counter()
+    oracle.mixed_ir(m.lower, m.upper_addr, dg, up, case.b, tol=1e-8, max_iter=2, max_outer=1)
+    t_a = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.mixed_ir(m.lower, m.upper_addr, dg, up, case.b, tol=1e-8, max_iter=2 + n_inner_sample, max_outer=1)
+    t_b = time.perf_counter() - t0
+    per_inner = (t_b - t_a) / n_inner_sample
+    fixed = t_a - 2 * per_inner                           # factor + 2 residuals + setup
+    t0 = time.perf_counter()
+    oracle.amul(m.lower, m.upper_addr, dg, up, case.b)
+    t_res = time.perf_counter() - t0
+    proj = t_asm + fixed + max(0, PROJECTION_ITERS["outer"] - 1) * t_res + PROJECTION_ITERS["inner"] * per_inner
+    sample = (f"oracle assembly + DIC factor + 2 FP64 residuals + {2 + n_inner_sample} FP32 inner iterations "
+              f"(two timed runs, per-iteration cost by difference), projected to "
+              f"{PROJECTION_ITERS['inner']} inner iterations and {PROJECTION_ITERS['outer']} outer steps")
+    return proj * 1e3, dict(sample=sample, per_inner_ms=per_inner * 1e3, assembly_ms=t_asm * 1e3,
+                            cpu_seconds=t_asm + t_a + t_b + t_res)
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    case = make_case(args.n)
+    cores = 1
+    vals = []
+    info = {}
+    for k in range(args.warmup + args.steps):
+        v, info = cpu_sample(case, max(2, args.cpu_iters // 2))
+        if k >= args.warmup:
+            vals.append(v)
+    vals.sort()
+    value = vals[len(vals) // 2]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (mixed)", "data": "synthetic",
+        "config": config_of(case, args),
+        "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle", "sample": info["sample"]},
+        "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(case, args):
+    m = case.mesh
+    return {"workload": f"{args.n}^3 jittered permuted hex mesh, log-normal gamma, DIC, tol 1e-8",
+            "cells": m.n_cells, "faces": m.n_faces, "precond": "DIC", "tolerance": 1e-8,
+            "l2": "inputs larger than L2 (workspace and per-iteration streams > 129 MB)"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2512_22215_gb300 import MIXED, LduMesh, SolverControls, lib
+    from paper_2512_22215_gb300.core import perf_tensor, read_perf
+
+    case = make_case(args.n)
+    m = case.mesh
+    N, F = m.n_cells, m.n_faces
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    M = LduMesh(m.lower, m.upper_addr, N, device=dev)
+    sf, cc, bcell, bsf, bcf, bg, bt = T(m.sf), T(m.c), T(m.bface_cell), T(m.bface_sf), T(m.bface_cf), \
+        T(case.bgamma), T(case.btype)
+    gamma, b = T(case.gamma), T(case.b)
+    x = torch.zeros(N, dtype=torch.float64, device=dev)
+    perf = perf_tensor(1, dev)
+    ctl_mixed = SolverControls(precond=2, precision=MIXED, tolerance=1e-8, inner_rel_tol=1e-4, max_outer=30)
+    ctl_f64 = SolverControls(precond=2, tolerance=1e-8)
+    s = torch.cuda.current_stream()
+
+    def step(ctl):
+        up, dg = M.assemble_laplacian(sf, cc, gamma, bcell, bsf, bcf, bg, bt)
+        x.zero_()
+        M.solve(dg, up, b, x, ctl, perf=perf)
+        return up, dg
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------------------------------------------------------- warm-up
+    for _ in range(max(3, args.warmup)):
+        up, dg = step(ctl_mixed)
+    barrier()
+    p_mixed = read_perf(perf)[0]
+
+    # ------------------------------------------------------------ timed region
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    barrier()
+    n0 = lib().spuma_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        step(ctl_mixed)
+    e1.record(s)
+    barrier()
+    launches = lib().spuma_launch_count() - n0
+    ms_step = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    ms_step_max = reduce_max(ms_step, world, dev)
+
+    # solve kernel alone (mixed and FP64), CUDA events around the launch
+    def time_solve(ctl, reps):
+        ts = []
+        for _ in range(reps):
+            x.zero_()
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            M.solve(dg, up, b, x, ctl, perf=perf)
+            c.record(s)
+            c.synchronize()
+            ts.append(a.elapsed_time(c))
+        ts.sort()
+        return ts[len(ts) // 2], read_perf(perf)[0]
+
+    up, dg = M.assemble_laplacian(sf, cc, gamma, bcell, bsf, bcf, bg, bt)
+    solve_mixed_ms, p_mixed = time_solve(ctl_mixed, max(3, args.steps))
+    solve_f64_ms, p_f64 = time_solve(ctl_f64, max(3, args.steps))
+    # assembly + FP64 solve per step (the comparison arm of the metric)
+    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(args.steps):
+        step(ctl_f64)
+    c.record(s)
+    c.synchronize()
+    f64_step_ms = a.elapsed_time(c) / args.steps
+
+    # stand-alone Amul on the prepared matrix (the PCG's Amul phase)
+    M.prepare(dg, up, 2)
+    xi = M.to_internal(b)
+    yi = torch.empty_like(xi)
+    xi32, yi32 = xi.float(), torch.empty(N, dtype=torch.float32, device=dev)
+
+    def time_amul(xv, yv, reps=20):
+        for _ in range(3):
+            M.amul_prepared(xv, yv)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a_, c_ in ev:
+            a_.record(s)
+            M.amul_prepared(xv, yv)
+            c_.record(s)
+        torch.cuda.synchronize()
+        ts = sorted(a_.elapsed_time(c_) for a_, c_ in ev)
+        return ts[len(ts) // 2] * 1e3   # us
+
+    amul64_us = time_amul(xi, yi)
+    amul32_us = time_amul(xi32, yi32)
+
+    # ----------------------------------------------------- end to end (host)
+    gamma_h = torch.from_numpy(case.gamma).pin_memory()
+    b_h = torch.from_numpy(case.b).pin_memory()
+    x_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    perf_h = torch.empty(perf.numel(), dtype=torch.uint8).pin_memory()
+    gamma_d, b_d = torch.empty_like(gamma), torch.empty_like(b)
+
+    def e2e_step():
+        gamma_d.copy_(gamma_h, non_blocking=True)
+        b_d.copy_(b_h, non_blocking=True)
+        u2, d2 = M.assemble_laplacian(sf, cc, gamma_d, bcell, bsf, bcf, bg, bt)
+        x.zero_()
+        M.solve(d2, u2, b_d, x, ctl_mixed, perf=perf)
+        x_h.copy_(x, non_blocking=True)
+        perf_h.copy_(perf, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s)
+    for _ in range(args.steps):
+        e2e_step()
+    c.record(s)
+    c.synchronize()
+    e2e_ms = reduce_max(a.elapsed_time(c) / args.steps, world, dev)
+    h2d = gamma_h.numel() * 8 + b_h.numel() * 8
+    d2h = x_h.numel() * 8 + perf_h.numel()
+
+    # -------------------------------------------------------------- roofline
+    wb = workload_bytes(N, F)
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    mixed_bytes = p_mixed["n_iter"] * wb["it32"] + (p_mixed["n_outer"] + 1) * wb["resid64"]
+    achieved = mixed_bytes / (solve_mixed_ms * 1e-3) / 1e9
+    f64_bytes = p_f64["n_iter"] * wb["it64"]
+    roofline = {"kernel": "k_solve (persistent mixed-precision solve, one launch per solve)", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "peak_kind": peak_kind, "traffic": None,
+                "algorithmic_bytes": int(mixed_bytes),
+                "basis": "inner iterations x (76N + 36F) + (outer + 1) FP64 residuals x (16F + 40N)"}
+
+    line = {
+        "metric": METRIC, "value": round(ms_step_max, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step_max, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (mixed)", "data": "synthetic",
+        "config": config_of(case, args),
+        "step": "laplacian assembly + mixed-precision DIC-PCG solve to 1e-8",
+        "mixed": {"solve_ms": round(solve_mixed_ms, 3), "inner_iters": p_mixed["n_iter"],
+                  "outer": p_mixed["n_outer"], "final_residual": p_mixed["final_residual"],
+                  "converged": p_mixed["converged"]},
+        "fp64": {"solve_ms": round(solve_f64_ms, 3), "step_ms": round(f64_step_ms, 3), "iters": p_f64["n_iter"],
+                 "final_residual": p_f64["final_residual"], "converged": p_f64["converged"],
+                 "achieved_gbs": round(f64_bytes / (solve_f64_ms * 1e-3) / 1e9, 1)},
+        "mixed_speedup_vs_fp64": round(solve_f64_ms / solve_mixed_ms, 3),
+        "amul": {"f64_us": round(amul64_us, 2), "f64_gbs_ldu": round(wb["amul64"] / amul64_us / 1e3, 1),
+                 "f64_frac_ldu": round(wb["amul64"] / amul64_us / 1e3 / hbm, 4),
+                 "f32_us": round(amul32_us, 2), "f32_gbs_ldu": round(wb["amul32"] / amul32_us / 1e3, 1),
+                 "basis": "LDU algorithmic bytes 16F + 24N (FP64), 12F + 12N (FP32)"},
+        "n_levels": M.n_levels,
+        "roofline": roofline,
+        "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "api": "spuma_assemble_laplacian + spuma_pcg_solve with gamma and b copied from pinned host "
+                       "memory and x and the solver report copied back, every step"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu:
+        cpu_ms, info = cpu_sample(case, args.cpu_iters)
+        line["cpu_baseline"] = {"value": round(cpu_ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+                                "sample": info["sample"], "per_inner_iteration_ms": round(info["per_inner_ms"], 1),
+                                "cpu_seconds": round(info["cpu_seconds"], 1),
+                                "coe": round(cpu_ms / ms_step_max, 1)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -74,7 +74,8 @@ class Mesh:
 
 
 def _tri_geometry(p0, p1, p2, p3):
-    """Area vector and centre of quads given as 4 corner arrays [...,3]."""
+    """Area vector and centre of quads given as 4 corner arrays [...,3]
+    (component-wise arithmetic; returns arrays [...,3])."""
     ctil = 0.25 * (((p0 + p1) + p2) + p3)
     corners = (p0, p1, p2, p3)
     s = np.zeros_like(p0)
@@ -83,9 +84,14 @@ def _tri_geometry(p0, p1, p2, p3):
     for k in range(4):
         a = corners[k]
         b = corners[(k + 1) % 4]
-        at = 0.5 * np.cross(b - a, ctil - a)
+        e = b - a
+        q = ctil - a
+        at = np.empty_like(e)
+        at[..., 0] = 0.5 * (e[..., 1] * q[..., 2] - e[..., 2] * q[..., 1])
+        at[..., 1] = 0.5 * (e[..., 2] * q[..., 0] - e[..., 0] * q[..., 2])
+        at[..., 2] = 0.5 * (e[..., 0] * q[..., 1] - e[..., 1] * q[..., 0])
         ct = (a + b + ctil) / 3.0
-        mag = np.sqrt(np.einsum("...i,...i->...", at, at))
+        mag = np.sqrt(at[..., 0] ** 2 + at[..., 1] ** 2 + at[..., 2] ** 2)
         s += at
         wsum += mag
         csum += mag[..., None] * ct
@@ -132,6 +138,7 @@ def hex_block(n, jitter: float = 0.0, permute: bool = False, seed: int = 0,
     Sy, Cy = _tri_geometry(P[:-1, :, :-1], P[1:, :, :-1], P[1:, :, 1:], P[:-1, :, 1:])
     # normal to z: at k = 0..nz; +z normal
     Sz, Cz = _tri_geometry(P[:, :-1, :-1], P[:, :-1, 1:], P[:, 1:, 1:], P[:, 1:, :-1])
+    del P
 
     # cell centres and volumes (natural order, index [k, j, i])
     faces_out = [(-Sx[:, :, :-1], Cx[:, :, :-1]), (Sx[:, :, 1:], Cx[:, :, 1:]),
@@ -140,39 +147,77 @@ def hex_block(n, jitter: float = 0.0, permute: bool = False, seed: int = 0,
     ctil = sum(cf for _, cf in faces_out) / 6.0
     vol = np.zeros((nz, ny, nx))
     vc = np.zeros((nz, ny, nx, 3))
-    for s, cf in faces_out:
-        pv = np.einsum("...i,...i->...", s, cf - ctil) / 3.0
+    for sfo, cf in faces_out:
+        dc = cf - ctil
+        pv = (sfo[..., 0] * dc[..., 0] + sfo[..., 1] * dc[..., 1] + sfo[..., 2] * dc[..., 2]) / 3.0
         pc = 0.75 * cf + 0.25 * ctil
         vol += pv
         vc += pv[..., None] * pc
     cc = vc / vol[..., None]
+    del faces_out, ctil, vc
 
-    nat = np.arange(N, dtype=np.int64).reshape(nz, ny, nx)
     if permute:
         perm = rng.permutation(N).astype(np.int64)   # perm[old] = new id
     else:
         perm = np.arange(N, dtype=np.int64)
-    newid = perm[nat]
+    newid = perm.reshape(nz, ny, nx)
 
-    # internal faces (owner on the - side, S points - to +)
-    own = [newid[:, :, :-1][:, :, :], newid[:, :-1, :], newid[:-1]]
-    own = [newid[:, :, :-1], newid[:, :-1, :], newid[:-1, :, :]]
-    nei = [newid[:, :, 1:], newid[:, 1:, :], newid[1:, :, :]]
-    sfi = [Sx[:, :, 1:-1], Sy[:, 1:-1, :], Sz[1:-1]]
-    cfi = [Cx[:, :, 1:-1], Cy[:, 1:-1, :], Cz[1:-1]]
-    o = np.concatenate([a.ravel() for a in own])
-    nb = np.concatenate([a.ravel() for a in nei])
-    sf = np.concatenate([a.reshape(-1, 3) for a in sfi])
-    cf = np.concatenate([a.reshape(-1, 3) for a in cfi])
-    lo = np.minimum(o, nb)
-    up = np.maximum(o, nb)
-    swap = o > nb
-    sf[swap] = -sf[swap]
-    order = np.lexsort((up, lo))
-    lo = lo[order].astype(np.int32)
-    up = up[order].astype(np.int32)
-    sf = np.ascontiguousarray(sf[order])
-    cf = np.ascontiguousarray(cf[order])
+    # global face numbering: Sx flattened, then Sy, then Sz
+    nfx, nfy = Sx[..., 0].size, Sy[..., 0].size
+    fid_x = np.arange(nfx, dtype=np.int64).reshape(nz, ny, nx + 1)
+    fid_y = nfx + np.arange(nfy, dtype=np.int64).reshape(nz, ny + 1, nx)
+    fid_z = nfx + nfy + np.arange(Sz[..., 0].size, dtype=np.int64).reshape(nz + 1, ny, nx)
+    S_all = [np.concatenate([Sx[..., d].ravel(), Sy[..., d].ravel(), Sz[..., d].ravel()]) for d in range(3)]
+    C_all = [np.concatenate([Cx[..., d].ravel(), Cy[..., d].ravel(), Cz[..., d].ravel()]) for d in range(3)]
+
+    # per cell (natural index) its 6 neighbours and faces: x-, x+, y-, y+, z-, z+
+    BIG = np.int64(np.iinfo(np.int64).max)
+    nb = np.full((nz, ny, nx, 6), BIG, dtype=np.int64)
+    fc = np.zeros((nz, ny, nx, 6), dtype=np.int64)
+    sg = np.zeros((nz, ny, nx, 6), dtype=np.int8)
+    nb[:, :, 1:, 0] = newid[:, :, :-1]
+    nb[:, :, :-1, 1] = newid[:, :, 1:]
+    nb[:, 1:, :, 2] = newid[:, :-1, :]
+    nb[:, :-1, :, 3] = newid[:, 1:, :]
+    nb[1:, :, :, 4] = newid[:-1]
+    nb[:-1, :, :, 5] = newid[1:]
+    fc[..., 0] = fid_x[:, :, :-1]
+    fc[..., 1] = fid_x[:, :, 1:]
+    fc[..., 2] = fid_y[:, :-1, :]
+    fc[..., 3] = fid_y[:, 1:, :]
+    fc[..., 4] = fid_z[:-1]
+    fc[..., 5] = fid_z[1:]
+    sg[..., 0::2] = -1      # face on the cell's minus side: stored S points towards the cell
+    sg[..., 1::2] = 1
+    nb = nb.reshape(N, 6)
+    fc = fc.reshape(N, 6)
+    sg = sg.reshape(N, 6)
+    # rows in new-id order; keep only neighbours with a larger id (this cell is "lower")
+    rows = np.empty_like(nb)
+    rows[perm] = nb
+    fcr = np.empty_like(fc)
+    fcr[perm] = fc
+    sgr = np.empty_like(sg)
+    sgr[perm] = sg
+    del nb, fc, sg
+    own = np.arange(N, dtype=np.int64)[:, None]
+    rows[rows <= own] = BIG
+    order = np.argsort(rows, axis=1, kind="stable")
+    rows = np.take_along_axis(rows, order, axis=1)
+    fcr = np.take_along_axis(fcr, order, axis=1)
+    sgr = np.take_along_axis(sgr, order, axis=1)
+    valid = rows != BIG
+    up = rows[valid].astype(np.int32)
+    lo = np.broadcast_to(own, rows.shape)[valid].astype(np.int32)
+    fsel = fcr[valid]
+    sgn = sgr[valid].astype(np.float64)
+    del rows, fcr, sgr, valid, order
+    sf = np.empty((lo.shape[0], 3))
+    cf = np.empty((lo.shape[0], 3))
+    for d in range(3):
+        sf[:, d] = S_all[d][fsel] * sgn
+        cf[:, d] = C_all[d][fsel]
+    del S_all, C_all, fsel, sgn
 
     # boundary faces, patch order xmin, xmax, ymin, ymax, zmin, zmax
     bcell, bsf, bcf, bpatch = [], [], [], []
@@ -191,14 +236,15 @@ def hex_block(n, jitter: float = 0.0, permute: bool = False, seed: int = 0,
         bpatch.append(np.full(cid.size, pi, dtype=np.int8))
 
     cnew = np.empty((N, 3))
-    cnew[newid.ravel()] = cc.reshape(-1, 3)
+    cnew[perm] = cc.reshape(-1, 3)
     vnew = np.empty(N)
-    vnew[newid.ravel()] = vol.ravel()
+    vnew[perm] = vol.ravel()
     ijk = np.empty((N, 3), dtype=np.int32)
-    kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
-    ijk[newid.ravel(), 0] = ii.ravel()
-    ijk[newid.ravel(), 1] = jj.ravel()
-    ijk[newid.ravel(), 2] = kk.ravel()
+    kk, jj, ii = np.meshgrid(np.arange(nz, dtype=np.int32), np.arange(ny, dtype=np.int32),
+                             np.arange(nx, dtype=np.int32), indexing="ij")
+    ijk[perm, 0] = ii.ravel()
+    ijk[perm, 1] = jj.ravel()
+    ijk[perm, 2] = kk.ravel()
 
     mesh = Mesh(
         n_cells=N, n_faces=int(lo.shape[0]), lower=lo, upper_addr=up, sf=sf, cf=cf,

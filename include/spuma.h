@@ -1,0 +1,278 @@
+/*
+ * spuma.h -- C ABI of the GB300 LDU pressure-solve library.
+ *
+ * The library solves A x = b for the pressure equation of a finite-volume
+ * mesh stored in OpenFOAM's face-addressed LDU format ("LDUorderedCOO",
+ * paper Sec. 2.1): per internal face f an owner lower_addr[f] and a
+ * neighbour upper_addr[f] with lower_addr[f] < upper_addr[f], faces sorted by
+ * (lower, upper); coefficients diag[n_cells] and upper[n_faces] (the matrix
+ * is symmetric, so lower == upper).  Sign convention: A is the NEGATIVE of
+ * OpenFOAM's laplacian matrix, so A is symmetric positive definite
+ * (diag > 0, upper < 0).
+ *
+ * Conventions shared by every entry point
+ *  - All array arguments are DEVICE pointers (cudaMalloc'ed or torch tensor
+ *    storage on the current device), owned by the caller, unless stated
+ *    otherwise.  The library never allocates device memory: all scratch and
+ *    all derived topology live in the caller's workspace.
+ *  - stream is a cudaStream_t (passed as void*); NULL means the legacy
+ *    default stream.  Calls are asynchronous with respect to the host except
+ *    where stated.
+ *  - Arguments are checked on the host before anything is launched; a bad
+ *    argument returns an error status and launches nothing.
+ *  - Errors found on the device (non-finite input, a non-positive DIC pivot,
+ *    a grid-barrier timeout) never trap: they are written to the solver
+ *    report (spuma_solver_perf.status) on the device, and
+ *    spuma_ldu_device_status() reads them back.
+ *  - Non-convergence is not an error (OpenFOAM semantics): status OK with
+ *    converged == 0.
+ *  - Integers are int32: n_faces < 2^31.
+ */
+#ifndef SPUMA_H
+#define SPUMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spuma_ldu* spuma_ldu_t;
+typedef struct spuma_batch* spuma_batch_t;
+typedef void* spuma_stream_t;
+
+typedef enum {
+    SPUMA_OK = 0,
+    SPUMA_ERR_INVALID_ARG = 1,           /* NULL pointer, negative size, bad enum      */
+    SPUMA_ERR_NOT_UPPER_TRIANGULAR = 2,  /* l >= u, index out of range, faces unsorted */
+    SPUMA_ERR_CUDA = 3,                  /* a CUDA runtime call failed (see last error) */
+    SPUMA_ERR_WORKSPACE_TOO_SMALL = 4,
+    SPUMA_ERR_SINGULAR = 5,              /* |p.Ap| / normFactor < 1e-300               */
+    SPUMA_ERR_NOT_SPD = 6,               /* a DIC pivot is <= 0                         */
+    SPUMA_ERR_NONFINITE = 7,             /* NaN or Inf among the coefficients or b      */
+    SPUMA_ERR_DEVICE_TIMEOUT = 8         /* a grid barrier waited past its time limit   */
+} spuma_status;
+
+typedef enum { SPUMA_F64 = 0, SPUMA_MIXED = 1, SPUMA_F32 = 2 } spuma_precision;
+typedef enum { SPUMA_PRECOND_NONE = 0, SPUMA_PRECOND_DIAGONAL = 1, SPUMA_PRECOND_DIC = 2 } spuma_precond;
+
+/* Solver controls, after OpenFOAM's fvSolution entries (paper appendix,
+ * fvSolution listing: solver PCG, preconditioner, tolerance, relTol, maxIter,
+ * minIter).  Residuals are OpenFOAM's normalised L1 residual
+ * sum|b - A x| / normFactor.
+ *  precision SPUMA_MIXED: FP32 inner PCG inside FP64 iterative refinement;
+ *    inner_rel_tol is the inner solve's relative tolerance, max_outer the
+ *    maximum number of refinement steps; max_iter bounds each inner solve.
+ *  block_threads: 0 = library default (or the tuned value for batches).   */
+typedef struct {
+    int32_t precond;        /* spuma_precond                              */
+    int32_t precision;      /* spuma_precision (SPUMA_F32 only for Amul)  */
+    double tolerance;       /* absolute normalised residual               */
+    double rel_tol;         /* relative to the initial residual, 0 = off  */
+    double inner_rel_tol;   /* mixed form only                             */
+    int32_t max_iter;
+    int32_t min_iter;
+    int32_t max_outer;      /* mixed form only                             */
+    int32_t block_threads;
+} spuma_solver_controls;
+
+/* Solver report (OpenFOAM's solverPerformance), written to DEVICE memory by
+ * the solve so that solves can be queued and captured without a host sync. */
+typedef struct {
+    double initial_residual;
+    double final_residual;
+    int32_t n_iter;         /* PCG iterations (all inner iterations for MIXED) */
+    int32_t n_outer;        /* refinement steps (MIXED), else 0               */
+    int32_t converged;
+    int32_t singular;
+    int32_t status;         /* spuma_status of the device side                */
+    int32_t n_levels;       /* DIC level count used                           */
+} spuma_solver_perf;
+
+/* ------------------------------------------------------------------------
+ * Topology.  spuma_workspace_bytes() gives the size of the caller's device
+ * workspace for a mesh; spuma_ldu_create() builds, on the device, everything
+ * derived from the addressing (face-to-cell gather lists, the DIC level sets,
+ * the level-ordered internal layout) into it.  Create is SYNCHRONOUS (it
+ * reads the validation result and the level count back) and returns
+ * SPUMA_ERR_NOT_UPPER_TRIANGULAR unless 0 <= l(f) < u(f) < n_cells and the
+ * faces are sorted by (l, u) without duplicates.  The handle keeps pointers
+ * into the workspace, which must stay allocated and untouched until
+ * spuma_ldu_destroy().  The addressing arrays are copied; the caller may free
+ * them after create returns.  flags: reserved, pass 0.
+ * ---------------------------------------------------------------------- */
+size_t spuma_workspace_bytes(int32_t n_cells, int32_t n_faces, int32_t flags);
+spuma_status spuma_ldu_create(int32_t n_cells, int32_t n_faces, const int32_t* lower_addr,
+                              const int32_t* upper_addr, void* workspace, size_t workspace_bytes,
+                              spuma_stream_t stream, spuma_ldu_t* out);
+spuma_status spuma_ldu_destroy(spuma_ldu_t h);
+/* Host-side facts of a handle: cell and face count, DIC level count. */
+spuma_status spuma_ldu_info(spuma_ldu_t h, int32_t* n_cells, int32_t* n_faces, int32_t* n_levels);
+/* Synchronises the stream and returns the device-side status of the last
+ * operation on this handle (SPUMA_OK if none failed). */
+spuma_status spuma_ldu_device_status(spuma_ldu_t h, spuma_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Laplacian assembly, "Gauss linear corrected" (paper appendix, fvSchemes
+ * listing; "P assembly" rows of the scaling tables, Sec. 4.4).  Implicit part
+ * of A = -laplacian(gamma, p):
+ *   a_f = (gamma_f |S_f|) / max(n_f . d_f, 0.05 |d_f|),  n_f = S_f/|S_f|,
+ *   d_f = C[u(f)] - C[l(f)];  upper_f = -a_f;
+ *   diag_i = sum of a_f over the internal faces of i (face order), then plus
+ *   a_b = (gamma_b |S_b|)/max(n_b . (Cb_b - C_i), 0.05 |Cb_b - C_i|) for each
+ *   Dirichlet boundary face b of cell i (type 1, value 0), in face order.
+ *   Zero-gradient faces (type 0) add nothing.
+ * Arithmetic order: |S| = sqrt((Sx Sx + Sy Sy) + Sz Sz), n.d =
+ * ((Sx dx + Sy dy) + Sz dz)/|S|, a = (gamma |S|)/max(n.d, 0.05 |d|), no
+ * fused multiply-add; the result is bit-identical to a sequential face loop.
+ * Layout: face_sf[F][3], cell_c[N][3], face_gamma[F]; boundary arrays
+ * bface_cell[B], bface_sf[B][3] (outward), bface_cf[B][3], bface_gamma[B],
+ * bface_type[B] (int8).  Outputs upper[F], diag[N] (FP64, original order).
+ * n_bfaces may be 0 (boundary pointers then may be NULL).
+ * ---------------------------------------------------------------------- */
+spuma_status spuma_assemble_laplacian(spuma_ldu_t h, const double* face_sf, const double* cell_c,
+                                      const double* face_gamma, int32_t n_bfaces,
+                                      const int32_t* bface_cell, const double* bface_sf,
+                                      const double* bface_cf, const double* bface_gamma,
+                                      const int8_t* bface_type, double* upper, double* diag,
+                                      spuma_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * lduMatrix::Amul (paper Sec. 4.2, profiling table "SpMVM (Amul + Tmul)"):
+ *   y_i = d_i x_i + sum_{f: u(f)=i} a_f x_{l(f)} + sum_{f: l(f)=i} a_f x_{u(f)}
+ * with the terms of row i taken in face order (neighbour-side faces
+ * ascending, then owner-side faces ascending), each a fused multiply-add:
+ * bit-identical to the sequential face loop y_u += a_f x_l; y_l += a_f x_u.
+ * No atomics: a face-to-cell gather.  precision SPUMA_F64: double arrays;
+ * SPUMA_F32: float arrays.  Vectors in the caller's (original) cell order.
+ * ---------------------------------------------------------------------- */
+spuma_status spuma_amul(spuma_ldu_t h, int32_t precision, const void* diag, const void* upper,
+                        const void* x, void* y, spuma_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Prepared matrix.  spuma_matrix_prepare() copies diag/upper into the
+ * handle's level-ordered internal layout (FP64 and FP32 copies) and, for
+ * SPUMA_PRECOND_DIC, computes the DIC factor
+ *   p_i = d_i - sum_{f: u(f)=i, ascending} (a_f a_f)/p_{l(f)},  rD_i = 1/p_i
+ * (paper Sec. 4.3, coarse-level DIC), level by level, bit-identical to the
+ * sequential face loop; for SPUMA_PRECOND_DIAGONAL rD_i = 1/d_i.
+ * spuma_pcg_solve() calls it itself; it is exposed for the Amul benchmark
+ * and the parity tests.
+ * spuma_read_rD() copies rD (FP64, original order) to rD_out.
+ * spuma_amul_prepared(): y = A x on the prepared matrix, vectors in the
+ * handle's internal (level) order, the exact kernel phase that PCG runs.
+ * spuma_permute(): dir 0 gathers original -> internal, 1 scatters back
+ * (FP64 vectors).
+ * spuma_precondition(): w = M^-1 r for the prepared preconditioner
+ * (original order, FP64):  w_i = rD_i r_i;  forward sweep, faces ascending:
+ * w_u -= (rD_u a_f) w_l;  backward sweep, faces descending:
+ * w_l -= (rD_l a_f) w_u;  each -= a fused multiply-add of the rounded
+ * product, bit-identical to the sequential sweeps.
+ * ---------------------------------------------------------------------- */
+spuma_status spuma_matrix_prepare(spuma_ldu_t h, const double* diag, const double* upper,
+                                  int32_t precond, spuma_stream_t stream);
+spuma_status spuma_read_rD(spuma_ldu_t h, double* rD_out, spuma_stream_t stream);
+spuma_status spuma_amul_prepared(spuma_ldu_t h, int32_t precision, const void* x_internal,
+                                 void* y_internal, spuma_stream_t stream);
+spuma_status spuma_permute(spuma_ldu_t h, int32_t dir, const double* src, double* dst,
+                           spuma_stream_t stream);
+spuma_status spuma_precondition(spuma_ldu_t h, int32_t precond, const double* r, double* w,
+                                spuma_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * PCG solve (paper appendix, fvSolution listing: PCG with DIC or diagonal
+ * preconditioning; OpenFOAM's PCG recurrences, sumProd/sumMag reductions):
+ *   q = A x; r = b - q; normFactor = sum(|q - s xbar| + |b - s xbar|) + 1e-20
+ *   (s = row sums, xbar = mean x); res0 = sum|r| / normFactor; then, if
+ *   min_iter > 0 or res0 is not converged, repeat
+ *     w = M^-1 r; rho = w.r; p = w (first) | w + (rho/rho_old) p;
+ *     q = A p; sigma = q.p (singular if |sigma|/normFactor < 1e-300);
+ *     alpha = rho/sigma; x += alpha p; r -= alpha q; res = sum|r|/normFactor
+ *   while (n_iter < max_iter and not converged) or n_iter < min_iter,
+ *   converged: res < tolerance or (rel_tol > 0 and res < rel_tol res0).
+ * x is the initial guess on entry and the solution on exit (original order).
+ * precision SPUMA_MIXED: FP32 coefficients, Amul and DIC sweeps inside FP64
+ * iterative refinement (FP64 residual, FP64 reductions, FP64 rD):
+ *   r = b - A x (FP64); stop when sum|r|/normFactor < tolerance or after
+ *   max_outer steps; s = max|r|; inner FP32 PCG on A d = r/s from d = 0 to
+ *   inner_rel_tol; x += s d.
+ * The whole solve is one persistent cooperative kernel (plus the prepare
+ * kernels): no host round trip per iteration.  perf is a DEVICE pointer.
+ * ---------------------------------------------------------------------- */
+spuma_status spuma_pcg_solve(spuma_ldu_t h, const double* diag, const double* upper,
+                             const double* b, double* x, const spuma_solver_controls* ctl,
+                             spuma_solver_perf* perf, spuma_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Adjoint of x = A^-1 b for a loss L(x), given x and dldx = dL/dx:
+ *   A lambda = dldx (A symmetric: A^T = A, same PCG, lambda from 0);
+ *   dL/db = lambda;  dL/dupper_f = -(lambda_{l(f)} x_{u(f)} + lambda_{u(f)} x_{l(f)});
+ *   dL/ddiag_i = -lambda_i x_i  (dlddiag may be NULL).
+ * x is taken as given (recomputed by the caller's forward), no Krylov
+ * history is kept.  Outputs in original order: dldb[N], dldupper[F].
+ * ---------------------------------------------------------------------- */
+spuma_status spuma_pcg_adjoint(spuma_ldu_t h, const double* diag, const double* upper,
+                               const double* x, const double* dldx, double* dldb,
+                               double* dldupper, double* dlddiag, const spuma_solver_controls* ctl,
+                               spuma_solver_perf* perf, spuma_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Batched solve: n_sys independent systems (each with its own handle and
+ * workspace) in ONE persistent cooperative launch; each system converges on
+ * its own (per-system device-side convergence) with the controls *ctl.
+ * Arrays of n_sys DEVICE pointers are passed as HOST arrays; perf[n_sys] is
+ * device memory.  spuma_batch_create() records the pointers, picks the block
+ * size and the split of the grid between systems with the library's
+ * autotuner (timed trial solves on the stream, cached per problem signature
+ * in memory and, when SPUMA_TUNE_CACHE names a file, in that JSON file),
+ * and captures the launch in a CUDA graph; spuma_batch_run() replays it.
+ * spuma_batch_solve() is the one-shot form (no graph, no tuning).
+ * ---------------------------------------------------------------------- */
+spuma_status spuma_batch_create(int32_t n_sys, const spuma_ldu_t* hs, const double* const* diag,
+                                const double* const* upper, const double* const* b,
+                                double* const* x, const spuma_solver_controls* ctl,
+                                spuma_solver_perf* perf, int32_t autotune, spuma_stream_t stream,
+                                spuma_batch_t* out);
+spuma_status spuma_batch_run(spuma_batch_t bt, spuma_stream_t stream);
+spuma_status spuma_batch_info(spuma_batch_t bt, int32_t* block_threads, int32_t* grid_blocks,
+                              double* tuned_ms);
+spuma_status spuma_batch_destroy(spuma_batch_t bt);
+spuma_status spuma_batch_solve(int32_t n_sys, const spuma_ldu_t* hs, const double* const* diag,
+                               const double* const* upper, const double* const* b,
+                               double* const* x, const spuma_solver_controls* ctl,
+                               spuma_solver_perf* perf, spuma_stream_t stream);
+
+/* Host-only helpers of the batch autotuner (no device work).
+ * spuma_batch_split: split grid blocks between n_sys systems in proportion to
+ * weights[], at least one block each, largest-remainder rounding; writes
+ * split_out[0..n_sys] (block ranges) and returns 1, or 0 when grid < n_sys.
+ * spuma_tune_cache_lookup / _store: the tuner's cache, kept in memory and,
+ * when path is not NULL or empty, in a JSON file whose lines read
+ *   "signature": [block_threads, split_policy, milliseconds],
+ * Lookup returns 1 on a hit; store returns 1 on success.                   */
+int32_t spuma_batch_split(int32_t n_sys, const double* weights, int32_t grid, int32_t* split_out);
+int32_t spuma_tune_cache_lookup(const char* path, const char* signature, int32_t* block_threads,
+                                int32_t* split_policy, double* ms);
+int32_t spuma_tune_cache_store(const char* path, const char* signature, int32_t block_threads,
+                               int32_t split_policy, double ms);
+
+/* ------------------------------------------------------------------------
+ * Diagnostics.
+ * spuma_status_string: static text of a status.  spuma_last_error: text of
+ * the last host-side error of the calling thread.  spuma_launch_count: the
+ * number of kernels this library has launched in the process (a counter on
+ * the host, for benchmarks).  spuma_set_barrier_timeout_ns: time limit of
+ * every device-side grid-barrier wait in later launches (default 2 s); a test
+ * sets it to 0 to check that an expired wait returns
+ * SPUMA_ERR_DEVICE_TIMEOUT instead of hanging.
+ * ---------------------------------------------------------------------- */
+const char* spuma_status_string(int32_t status);
+const char* spuma_last_error(void);
+uint64_t spuma_launch_count(void);
+void spuma_set_barrier_timeout_ns(uint64_t ns);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPUMA_H */

@@ -1,0 +1,207 @@
+"""Tensor-level wrappers around the C ABI: a mesh handle that owns its
+workspace tensor, solver controls, batched solves.  Marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import torch
+
+from ._lib import (F32, F64, MIXED, PERF_BYTES, PRECOND_DIC, Controls, Perf, SpumaError, check, lib, ptr,
+                   stream_ptr)
+
+
+@dataclass
+class SolverControls:
+    precond: int = PRECOND_DIC
+    precision: int = F64
+    tolerance: float = 1e-8
+    rel_tol: float = 0.0
+    inner_rel_tol: float = 1e-4
+    max_iter: int = 20000
+    min_iter: int = 0
+    max_outer: int = 30
+    block_threads: int = 0
+
+    def c(self) -> Controls:
+        return Controls(self.precond, self.precision, self.tolerance, self.rel_tol, self.inner_rel_tol,
+                        self.max_iter, self.min_iter, self.max_outer, self.block_threads)
+
+
+def perf_tensor(n: int = 1, device="cuda") -> torch.Tensor:
+    return torch.zeros(n * PERF_BYTES, dtype=torch.uint8, device=device)
+
+
+def read_perf(t: torch.Tensor) -> list[dict]:
+    raw = t.cpu().numpy().tobytes()
+    out = []
+    for k in range(len(raw) // PERF_BYTES):
+        p = Perf.from_buffer_copy(raw[k * PERF_BYTES:(k + 1) * PERF_BYTES])
+        out.append({f: getattr(p, f) for f, _ in Perf._fields_})
+    return out
+
+
+class LduMesh:
+    """A mesh's LDU addressing on the device plus the library workspace."""
+
+    def __init__(self, lower, upper_addr, n_cells: int, device="cuda"):
+        L = lib()
+        dev = torch.device(device)
+        lower = torch.as_tensor(lower, dtype=torch.int32).to(dev).contiguous()
+        upper_addr = torch.as_tensor(upper_addr, dtype=torch.int32).to(dev).contiguous()
+        self.n_cells = int(n_cells)
+        self.n_faces = int(lower.numel())
+        self.device = dev
+        nbytes = L.spuma_workspace_bytes(self.n_cells, self.n_faces, 0)
+        # 256-byte alignment: the caching allocator returns 512-byte aligned blocks
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        h = C.c_void_p()
+        st = L.spuma_ldu_create(self.n_cells, self.n_faces, ptr(lower), ptr(upper_addr), self._ws_ptr, nbytes,
+                                stream_ptr(), C.byref(h))
+        check(st, "spuma_ldu_create")
+        self.handle = h
+        self.lower = lower
+        self.upper_addr = upper_addr
+        n, f, lv = C.c_int32(), C.c_int32(), C.c_int32()
+        check(L.spuma_ldu_info(h, C.byref(n), C.byref(f), C.byref(lv)), "spuma_ldu_info")
+        self.n_levels = lv.value
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                lib().spuma_ldu_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    # ------------------------------------------------------------ ops ----
+    def device_status(self) -> int:
+        return lib().spuma_ldu_device_status(self.handle, stream_ptr())
+
+    def assemble_laplacian(self, sf, c, gamma, bface_cell=None, bface_sf=None, bface_cf=None, bgamma=None,
+                           btype=None):
+        upper = torch.empty(self.n_faces, dtype=torch.float64, device=self.device)
+        diag = torch.empty(self.n_cells, dtype=torch.float64, device=self.device)
+        nb = 0 if bface_cell is None else int(bface_cell.numel())
+        check(lib().spuma_assemble_laplacian(self.handle, ptr(sf), ptr(c), ptr(gamma), nb, ptr(bface_cell),
+                                             ptr(bface_sf), ptr(bface_cf), ptr(bgamma), ptr(btype),
+                                             ptr(upper), ptr(diag), stream_ptr()), "spuma_assemble_laplacian")
+        return upper, diag
+
+    def amul(self, diag, upper, x, out=None):
+        prec = F32 if x.dtype == torch.float32 else F64
+        y = out if out is not None else torch.empty_like(x)
+        check(lib().spuma_amul(self.handle, prec, ptr(diag), ptr(upper), ptr(x), ptr(y), stream_ptr()),
+              "spuma_amul")
+        return y
+
+    def prepare(self, diag, upper, precond=PRECOND_DIC):
+        check(lib().spuma_matrix_prepare(self.handle, ptr(diag), ptr(upper), int(precond), stream_ptr()),
+              "spuma_matrix_prepare")
+
+    def read_rD(self):
+        out = torch.empty(self.n_cells, dtype=torch.float64, device=self.device)
+        check(lib().spuma_read_rD(self.handle, ptr(out), stream_ptr()), "spuma_read_rD")
+        return out
+
+    def amul_prepared(self, x_internal, out=None):
+        prec = F32 if x_internal.dtype == torch.float32 else F64
+        y = out if out is not None else torch.empty_like(x_internal)
+        check(lib().spuma_amul_prepared(self.handle, prec, ptr(x_internal), ptr(y), stream_ptr()),
+              "spuma_amul_prepared")
+        return y
+
+    def to_internal(self, v):
+        out = torch.empty_like(v)
+        check(lib().spuma_permute(self.handle, 0, ptr(v), ptr(out), stream_ptr()), "spuma_permute")
+        return out
+
+    def from_internal(self, v):
+        out = torch.empty_like(v)
+        check(lib().spuma_permute(self.handle, 1, ptr(v), ptr(out), stream_ptr()), "spuma_permute")
+        return out
+
+    def precondition(self, r, precond=PRECOND_DIC):
+        w = torch.empty_like(r)
+        check(lib().spuma_precondition(self.handle, int(precond), ptr(r), ptr(w), stream_ptr()),
+              "spuma_precondition")
+        return w
+
+    def solve(self, diag, upper, b, x=None, controls: SolverControls | None = None, perf=None, check_status=True):
+        """Solve A x = b in place of x (x0 = 0 when x is None).  Returns (x, perf dict | perf tensor)."""
+        ctl = (controls or SolverControls()).c()
+        if x is None:
+            x = torch.zeros_like(b)
+        own_perf = perf is None
+        if own_perf:
+            perf = perf_tensor(1, self.device)
+        check(lib().spuma_pcg_solve(self.handle, ptr(diag), ptr(upper), ptr(b), ptr(x), C.byref(ctl), ptr(perf),
+                                    stream_ptr()), "spuma_pcg_solve")
+        if not own_perf:
+            return x, perf
+        p = read_perf(perf)[0]
+        if check_status and p["status"] != 0:
+            raise SpumaError(p["status"], "device-side status of spuma_pcg_solve")
+        return x, p
+
+    def adjoint(self, diag, upper, x, dldx, controls: SolverControls | None = None, want_diag=True,
+                check_status=True):
+        ctl = (controls or SolverControls(tolerance=1e-12)).c()
+        dldb = torch.empty_like(dldx)
+        dldu = torch.empty(self.n_faces, dtype=torch.float64, device=self.device)
+        dldd = torch.empty_like(dldx) if want_diag else None
+        perf = perf_tensor(1, self.device)
+        check(lib().spuma_pcg_adjoint(self.handle, ptr(diag), ptr(upper), ptr(x), ptr(dldx), ptr(dldb), ptr(dldu),
+                                      ptr(dldd), C.byref(ctl), ptr(perf), stream_ptr()), "spuma_pcg_adjoint")
+        p = read_perf(perf)[0]
+        if check_status and p["status"] != 0:
+            raise SpumaError(p["status"], "device-side status of spuma_pcg_adjoint")
+        return dldb, dldu, dldd, p
+
+
+class BatchSolve:
+    """Many systems in one persistent launch, replayed from a CUDA graph."""
+
+    def __init__(self, meshes, diags, uppers, bs, xs, controls: SolverControls | None = None, autotune=True):
+        n = len(meshes)
+        self.meshes, self.diags, self.uppers, self.bs, self.xs = meshes, diags, uppers, bs, xs
+        self.ctl = (controls or SolverControls()).c()
+        self.perf = perf_tensor(n, meshes[0].device)
+        H = (C.c_void_p * n)(*[m.handle.value for m in meshes])
+        arr = lambda ts: (C.c_void_p * n)(*[ptr(t) for t in ts])
+        self._keep = (H, arr(diags), arr(uppers), arr(bs), arr(xs))
+        h = C.c_void_p()
+        check(lib().spuma_batch_create(n, self._keep[0], self._keep[1], self._keep[2], self._keep[3], self._keep[4],
+                                       C.byref(self.ctl), ptr(self.perf), 1 if autotune else 0, stream_ptr(),
+                                       C.byref(h)), "spuma_batch_create")
+        self.handle = h
+        t, g, ms = C.c_int32(), C.c_int32(), C.c_double()
+        check(lib().spuma_batch_info(h, C.byref(t), C.byref(g), C.byref(ms)), "spuma_batch_info")
+        self.block_threads, self.grid_blocks, self.tuned_ms = t.value, g.value, ms.value
+
+    def run(self):
+        check(lib().spuma_batch_run(self.handle, stream_ptr()), "spuma_batch_run")
+
+    def results(self):
+        return read_perf(self.perf)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                lib().spuma_batch_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def solve_host(mesh: LduMesh, diag, upper, b_host, controls: SolverControls | None = None):
+    """End-to-end call with host buffers: copies b (pinned host) in, solves,
+    copies x back.  Returns (x_host, perf dict)."""
+    b = b_host.to(mesh.device, non_blocking=True)
+    x = torch.zeros_like(b)
+    x, p = mesh.solve(diag, upper, b, x, controls)
+    return x.cpu(), p

@@ -1,0 +1,251 @@
+// common.cuh -- shared device helpers, the handle and the workspace layout of
+// the LDU pressure-solve library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include <string>
+#include <vector>
+
+#include "../../include/spuma.h"
+
+namespace spuma {
+
+constexpr int kMaxBlocks = 4096;       // partial-sum slots per reduction
+constexpr int kSlots = 8;              // reduction slots
+constexpr int kMaxBatch = 1024;        // systems per batched launch
+constexpr int kWarp = 32;
+
+// ---------------------------------------------------------------- errors --
+void set_error(const std::string& msg);
+spuma_status cuda_fail(cudaError_t e, const char* what);
+void count_launch(uint64_t n = 1);
+uint64_t barrier_timeout_ns();
+
+#define SPUMA_CUDA(call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// Device status words (int32): [0] status, [1] first offending cell/face.
+enum DevStatus { DS_STATUS = 0, DS_INDEX = 1, DS_LEVELS_CHANGED = 2, DS_MAXLEVEL = 3 };
+
+__device__ __forceinline__ void flag_error(int* st, int code, int index)
+{
+    if (atomicCAS(st + DS_STATUS, 0, code) == 0) st[DS_INDEX] = index;
+}
+
+// ------------------------------------------------------- memory helpers --
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned long long global_timer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ int ld_volatile_int(const int* p)
+{
+    return *(const volatile int*)p;
+}
+
+// Fused multiply-add in the working precision.
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
+// --------------------------------------------------------- grid barrier --
+// A group of co-resident blocks (a cooperative launch guarantees residency)
+// synchronises on an arrival counter and a generation word that sit on
+// separate 128-byte lines.  Every wait is bounded by a time limit: when it
+// expires the block records SPUMA_ERR_DEVICE_TIMEOUT and the caller unwinds.
+struct Group {
+    unsigned* count;       // arrival counter
+    unsigned* gen;         // generation
+    int* status;           // device status words
+    int nblocks;           // blocks in the group
+    int bid;               // this block's index in the group
+    unsigned long long timeout_ns;
+};
+
+// Returns true when the caller may continue (no error recorded anywhere).
+__device__ __forceinline__ bool group_sync(const Group& g)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned gen0 = ld_acquire(g.gen);
+        __threadfence();
+        unsigned arrived = atom_add_acq_rel(g.count, 1u);
+        if (arrived == (unsigned)g.nblocks - 1u) {
+            *(volatile unsigned*)g.count = 0u;
+            __threadfence();
+            st_release(g.gen, gen0 + 1u);
+        } else {
+            unsigned long long t0 = global_timer_ns();
+            while (ld_acquire(g.gen) == gen0) {
+                if (ld_volatile_int(g.status) != 0) break;
+                if (global_timer_ns() - t0 > g.timeout_ns) {
+                    flag_error(g.status, SPUMA_ERR_DEVICE_TIMEOUT, g.bid);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ld_volatile_int(g.status) == 0;
+}
+
+// ------------------------------------------------------------ reductions --
+// Block-level sums of NV doubles, written as this block's partials; after a
+// group_sync every block reads all partials of a slot in the same fixed order,
+// so the grid-wide result is deterministic and identical in every block.
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* partials, int slot0, int bid)
+{
+    __shared__ double red[NV][32];
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double s = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        v[k] = s;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) red[k][warp] = v[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            double s = lane < nw ? red[k][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) partials[(size_t)(slot0 + k) * kMaxBlocks + bid] = s;
+        }
+    }
+}
+
+template <int NV>
+__device__ __forceinline__ void block_max_store(double (&v)[NV], double* partials, int slot0, int bid)
+{
+    __shared__ double redm[NV][32];
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double s = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+        v[k] = s;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) redm[k][warp] = v[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            double s = lane < nw ? redm[k][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+            if (lane == 0) partials[(size_t)(slot0 + k) * kMaxBlocks + bid] = s;
+        }
+    }
+}
+
+// Grid-wide value of slot0..slot0+NV-1 (sum or max), broadcast to the block.
+template <int NV, bool MAX = false>
+__device__ __forceinline__ void grid_reduce_read(double (&out)[NV], const double* partials, int slot0, int nblocks)
+{
+    __shared__ double bc[NV];
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            const volatile double* ps = partials + (size_t)(slot0 + k) * kMaxBlocks;
+            double s = 0.0;
+            for (int j = lane; j < nblocks; j += 32) s = MAX ? fmax(s, ps[j]) : s + ps[j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                double t = __shfl_xor_sync(0xffffffffu, s, o);
+                s = MAX ? fmax(s, t) : s + t;
+            }
+            if (lane == 0) bc[k] = s;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; k++) out[k] = bc[k];
+    __syncthreads();
+}
+
+// ------------------------------------------------------- internal matrix --
+template <class T>
+struct Mat {
+    const int* Lptr;   // [n+1] lower (neighbour-side) entries of each row
+    const int* Lcol;   // internal column
+    const T* La;       // a_f
+    const T* Lc;       // rD_row * a_f   (DIC sweep coefficient)
+    const int* Uptr;   // [n+1] upper (owner-side) entries of each row
+    const int* Ucol;
+    const T* Ua;
+    const T* Uc;
+    const T* d;        // diagonal
+    const T* rD;       // DIC / diagonal reciprocal
+};
+
+// Workspace layout: one carve function used for sizing and for create.
+struct Layout {
+    size_t bytes = 0;
+    // topology (int32)
+    size_t perm, iperm, lvl, Lptr, Uptr, Lcol, Ucol, Lface, Uface;
+    size_t own_start, lo_start, lo_face, lo_col, laddr, uaddr;
+    // matrix
+    size_t La64, Ua64, Lc64, Uc64, d64, rD64;
+    size_t La32, Ua32, Lc32, Uc32, d32, rD32;
+    // vectors
+    size_t x64, r64, w64, p64, q64, b64;
+    size_t x32, r32, w32, p32, q32;
+    // control
+    size_t partials, bar, status, args;
+};
+
+Layout make_layout(int64_t n, int64_t nf);
+
+}  // namespace spuma
+
+// Host-side handle.
+struct spuma_ldu {
+    int32_t n = 0, nf = 0, nlev = 0;
+    int device = 0;
+    int num_sms = 0;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    spuma::Layout L;
+    int prepared_precond = -1;
+    std::vector<int32_t> h_lvl;
+    template <class T>
+    T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+};

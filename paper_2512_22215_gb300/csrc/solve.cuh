@@ -1,0 +1,45 @@
+// solve.cuh -- arguments of the persistent solver kernel (shared by the single
+// and the batched launch).
+#pragma once
+#include "common.cuh"
+
+namespace spuma {
+
+enum SolveMode { MODE_PREPARE = 0, MODE_SOLVE = 1, MODE_PRECONDITION = 2 };
+
+struct SolveArgs {
+    int n, nf, nlev;
+    int mode;              // SolveMode
+    int precond;           // spuma_precond
+    int precision;         // spuma_precision (F64 or MIXED)
+    int zero_x0;           // start from x = 0 instead of reading x_orig
+    int max_iter, min_iter, max_outer;
+    double tol, rel_tol, inner_rel_tol;
+    const int* lvl;        // [nlev+1] level starts (internal order)
+    const int* perm;       // internal -> original
+    // original-order inputs/outputs
+    const double* diag_orig;
+    const double* upper_orig;
+    const double* b_orig;
+    double* x_orig;
+    // internal matrix
+    const int *Lptr, *Lcol, *Lface, *Uptr, *Ucol, *Uface;
+    double *La64, *Ua64, *Lc64, *Uc64, *d64, *rD64;
+    float *La32, *Ua32, *Lc32, *Uc32, *d32, *rD32;
+    // internal vectors
+    double *x, *r, *w, *p, *q, *b;
+    float *xi, *ri, *wi, *pi, *qi;
+    // control
+    double* partials;
+    unsigned* bar;
+    int* status;
+    spuma_solver_perf* perf;
+};
+
+struct BatchTable {
+    int n_sys;
+    int split[257];                  // block ranges per system
+    const SolveArgs* args[256];      // device copies
+};
+
+}  // namespace spuma

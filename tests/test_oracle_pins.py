@@ -347,15 +347,22 @@ def test_adjoint_finite_differences():
 
 
 def test_pcg_norm_factor_shift_invariance():
-    """A (x + c) - s (xbar + c) = A x - s xbar for every constant c, so the
-    normalisation factor does not depend on the level of x; by the triangle
-    inequality it bounds the initial residual: |b - Ax| <= |b - t| + |Ax - t|."""
-    c, up, dg = case(4, jitter=0.2, permute=True, seed=19, lognormal_gamma=True)
+    """With zero row sums (all-Neumann boundary) A (x + c) - s (xbar + c) = A x - s xbar
+    for every constant c, so the normalisation factor does not depend on the
+    level of x.  With any boundary it bounds the initial residual (triangle
+    inequality: |b - Ax| <= |b - t| + |Ax - t|) and the PCG's initial residual is
+    sum|b - A x0| over it."""
+    c = hexmesh.pressure_case(4, jitter=0.2, permute=True, seed=19, lognormal_gamma=True, dirichlet=())
     m = c.mesh
+    up, dg = oracle.assemble_laplacian(m, c.gamma, c.bgamma, c.btype)
     x = np.random.default_rng(6).standard_normal(m.n_cells)
     nf = oracle.norm_factor(m.lower, m.upper_addr, dg, up, x, c.b)
     for shift in (3.0, -40.0):
         assert oracle.norm_factor(m.lower, m.upper_addr, dg, up, x + shift, c.b) == pytest.approx(nf, rel=1e-12)
+    c, up, dg = case(4, jitter=0.2, permute=True, seed=19, lognormal_gamma=True)
+    m = c.mesh
+    x = 50.0 * np.random.default_rng(7).standard_normal(m.n_cells)
+    nf = oracle.norm_factor(m.lower, m.upper_addr, dg, up, x, c.b)
     r = c.b - oracle.amul(m.lower, m.upper_addr, dg, up, x)
     assert np.abs(r).sum() <= nf
     _, p = oracle.pcg(m.lower, m.upper_addr, dg, up, c.b, x0=x, tol=1e-30, max_iter=1)
