@@ -75,6 +75,9 @@ def _declare(L):
     L.oracle_mixed_ir.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _i32, _f64,
                                   _f64, _i32, _i32, _f64p]
     L.oracle_mixed_ir.restype = _i32
+    L.oracle_mixed_reliable.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _i32, _f64,
+                                        _f64, _f64, _i32, _f64p]
+    L.oracle_mixed_reliable.restype = _i32
     L.oracle_adjoint.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _i32, _f64,
                                  _i32, _f64p, _f64p, _f64p, _f64p]
     L.oracle_adjoint.restype = _i32
@@ -169,6 +172,19 @@ def mixed_ir(l, u, diag, upper, b, x0=None, precond=PRECOND_DIC, tol=1e-8, inner
     return x, dict(status=int(st), initial_residual=perf[0], final_residual=perf[1],
                    n_iter=int(perf[2]), singular=int(perf[3]), converged=int(perf[4]),
                    n_outer=int(perf[5]))
+
+
+def mixed_reliable(l, u, diag, upper, b, x0=None, precond=PRECOND_DIC, tol=1e-8, rel_tol=0.0, delta=0.1,
+                   max_iter=20000):
+    """FP32 PCG with reliable FP64 updates (residual replacement, no restart)."""
+    n = len(diag)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    perf = np.zeros(6)
+    st = lib().oracle_mixed_reliable(n, len(l), _c(l, np.int32), _c(u, np.int32), _c(diag, np.float64),
+                                     _c(upper, np.float64), _c(b, np.float64), x, int(precond), float(tol),
+                                     float(rel_tol), float(delta), int(max_iter), perf)
+    return x, dict(status=int(st), initial_residual=perf[0], final_residual=perf[1], n_iter=int(perf[2]),
+                   singular=int(perf[3]), converged=int(perf[4]), n_outer=int(perf[5]))
 
 
 def adjoint(l, u, diag, upper, x, g, precond=PRECOND_DIC, tol=1e-13, max_iter=20000):

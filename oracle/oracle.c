@@ -408,3 +408,107 @@ int32_t oracle_adjoint(int32_t n, int32_t nf, const int32_t* l, const int32_t* u
     for (int32_t i = 0; i < n; i++) ddiag[i] = -(lambda[i] * x[i]);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Mixed precision with reliable updates (residual replacement): the FP32    */
+/* PCG (FP32 coefficients, Amul, DIC sweeps and vectors; reductions in       */
+/* double; alpha, beta in double rounded to float) accumulates its           */
+/* correction xs in FP32; whenever its recursively updated residual has      */
+/* dropped below delta times the residual of the last update, or it claims    */
+/* convergence, or max_iter is reached, the FP64 solution takes x += xs, the  */
+/* true residual r = b - A64 x is recomputed in FP64 and replaces the FP32    */
+/* residual, and the search direction p is kept (no Krylov restart).         */
+/* The solve stops when that FP64 residual is converged (or max_iter).       */
+/* perf: [0] initial res, [1] final res (FP64), [2] iterations,              */
+/* [3] singular, [4] converged, [5] reliable updates                          */
+/* ------------------------------------------------------------------------ */
+int32_t oracle_mixed_reliable(int32_t n, int32_t nf, const int32_t* l, const int32_t* u,
+                              const double* diag, const double* upper, const double* b, double* x,
+                              int32_t precond, double tol, double rel_tol, double delta,
+                              int32_t max_iter, double* perf)
+{
+    size_t b64 = sizeof(double) * (size_t)(n > 0 ? n : 1);
+    size_t b32 = sizeof(float) * (size_t)(n > 0 ? n : 1);
+    size_t bf32 = sizeof(float) * (size_t)(nf > 0 ? nf : 1);
+    double* r64 = (double*)malloc(b64);
+    double* q64 = (double*)malloc(b64);
+    double* rD = (double*)malloc(b64);
+    float* d32 = (float*)malloc(b32);
+    float* u32 = (float*)malloc(bf32);
+    float* r = (float*)malloc(b32);
+    float* xs = (float*)malloc(b32);
+    float* w = (float*)malloc(b32);
+    float* p = (float*)malloc(b32);
+    float* q = (float*)malloc(b32);
+    float* rD32 = (float*)malloc(b32);
+    int32_t status = 0, it = 0, updates = 0, singular = 0;
+    double res0 = 0.0, res = 0.0;
+    memset(perf, 0, 6 * sizeof(double));
+
+    for (int32_t i = 0; i < n; i++) d32[i] = (float)diag[i];
+    for (int32_t f = 0; f < nf; f++) u32[f] = (float)upper[f];
+    if (precond == 2) {
+        if (oracle_dic_factor(n, nf, l, u, diag, upper, rD) >= 0) { status = -2; goto done; }
+    } else if (precond == 1) {
+        oracle_diag_reciprocal(n, diag, rD);
+    }
+    for (int32_t i = 0; i < n; i++) rD32[i] = (float)rD[i];
+
+    oracle_amul(n, nf, l, u, diag, upper, x, q64);
+    for (int32_t i = 0; i < n; i++) r64[i] = b[i] - q64[i];
+    double nfac = oracle_norm_factor(n, nf, l, u, diag, upper, x, b, q64);
+    res0 = sum_mag(n, r64) / nfac;
+    res = res0;
+    if (converged(res0, res0, tol, rel_tol)) goto done;
+    for (int32_t i = 0; i < n; i++) { r[i] = (float)r64[i]; xs[i] = 0.0f; }
+    double rupd = res0, rho = 1.0, rho_old;
+    for (;;) {
+        rho_old = rho;
+        if (precond == 2) oracle_dic_precondition_f32(n, nf, l, u, upper, rD, r, w);
+        else if (precond == 1) for (int32_t i = 0; i < n; i++) w[i] = rD32[i] * r[i];
+        else for (int32_t i = 0; i < n; i++) w[i] = r[i];
+        rho = sum_prod_f32(n, w, r);
+        if (it == 0) {
+            for (int32_t i = 0; i < n; i++) p[i] = w[i];
+        } else {
+            float beta = (float)(rho / rho_old);
+            for (int32_t i = 0; i < n; i++) p[i] = w[i] + beta * p[i];
+        }
+        oracle_amul_f32(n, nf, l, u, d32, u32, p, q);
+        double sigma = sum_prod_f32(n, q, p);
+        if (fabs(sigma) / nfac < 1e-300) { singular = 1; break; }
+        float alpha = (float)(rho / sigma);
+        for (int32_t i = 0; i < n; i++) {
+            xs[i] += alpha * p[i];
+            r[i] -= alpha * q[i];
+        }
+        it++;
+        double ress = sum_mag_f32(n, r) / nfac;
+        if (ress < delta * rupd || converged(ress, res0, tol, rel_tol) || it >= max_iter) {
+            for (int32_t i = 0; i < n; i++) { x[i] += (double)xs[i]; xs[i] = 0.0f; }
+            oracle_amul(n, nf, l, u, diag, upper, x, q64);
+            for (int32_t i = 0; i < n; i++) r64[i] = b[i] - q64[i];
+            res = sum_mag(n, r64) / nfac;
+            updates++;
+            if (converged(res, res0, tol, rel_tol) || it >= max_iter) break;
+            for (int32_t i = 0; i < n; i++) r[i] = (float)r64[i];
+            rupd = res;
+        }
+    }
+    if (singular) {   /* fold the pending correction in */
+        for (int32_t i = 0; i < n; i++) x[i] += (double)xs[i];
+        oracle_amul(n, nf, l, u, diag, upper, x, q64);
+        for (int32_t i = 0; i < n; i++) r64[i] = b[i] - q64[i];
+        res = sum_mag(n, r64) / nfac;
+    }
+done:
+    perf[0] = res0;
+    perf[1] = res;
+    perf[2] = (double)it;
+    perf[3] = (double)singular;
+    perf[4] = (double)converged(res, res0, tol, rel_tol);
+    perf[5] = (double)updates;
+    free(r64); free(q64); free(rD); free(d32); free(u32); free(r); free(xs);
+    free(w); free(p); free(q); free(rD32);
+    return status;
+}

@@ -306,6 +306,28 @@ def test_mixed_ir_reaches_fp64_solution():
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= kappa * 1e-10
 
 
+def test_mixed_reliable_converges_without_restart_penalty():
+    """Reliable updates keep the FP32 Krylov space: the FP64 residual reaches the
+    tolerance, the solution is the FP64 system's, and the iteration count stays
+    close to the FP64 PCG's (a restarted refinement needs many more)."""
+    c, up, dg = case(16, jitter=0.2, permute=True, seed=20, lognormal_gamma=True)
+    m = c.mesh
+    A = dense(m.lower, m.upper_addr, dg, up)
+    xs = np.linalg.solve(A, c.b)
+    _, p64 = oracle.pcg(m.lower, m.upper_addr, dg, up, c.b, tol=1e-10)
+    x, p = oracle.mixed_reliable(m.lower, m.upper_addr, dg, up, c.b, tol=1e-10, delta=0.1)
+    assert p["converged"] == 1 and p["n_outer"] >= 5
+    r = c.b - A @ x
+    assert np.abs(r).sum() / np.abs(c.b).sum() < 1e-10
+    assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= np.linalg.cond(A) * 1e-10
+    assert p["n_iter"] <= 1.15 * p64["n_iter"] + 2
+    _, pr = oracle.mixed_ir(m.lower, m.upper_addr, dg, up, c.b, tol=1e-10, inner_rel_tol=1e-4)
+    assert pr["n_iter"] > p["n_iter"]
+    # a tolerance already met: no iteration, no update
+    _, p0 = oracle.mixed_reliable(m.lower, m.upper_addr, dg, up, c.b, x0=xs, tol=1e-6)
+    assert p0["n_iter"] == 0 and p0["n_outer"] == 0
+
+
 # -------------------------------------------------------------- adjoint ----
 def test_adjoint_dense_and_identity():
     c = hexmesh.pressure_case(6, jitter=0.2, permute=True, seed=17, lognormal_gamma=True, with_target=True)
