@@ -213,7 +213,7 @@ def main():
     m = case.mesh
     N, F = m.n_cells, m.n_faces
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    M = LduMesh(m.lower, m.upper_addr, N, device=dev)
+    M = LduMesh(m.lower, m.upper_addr, N, device=dev, centres=m.c)
     sf, cc, bcell, bsf, bcf, bg, bt = T(m.sf), T(m.c), T(m.bface_cell), T(m.bface_sf), T(m.bface_cf), \
         T(case.bgamma), T(case.btype)
     gamma, b = T(case.gamma), T(case.b)

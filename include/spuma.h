@@ -106,6 +106,15 @@ size_t spuma_workspace_bytes(int32_t n_cells, int32_t n_faces, int32_t flags);
 spuma_status spuma_ldu_create(int32_t n_cells, int32_t n_faces, const int32_t* lower_addr,
                               const int32_t* upper_addr, void* workspace, size_t workspace_bytes,
                               spuma_stream_t stream, spuma_ldu_t* out);
+/* Same, with the cell centres cell_c[N][3] (device, FP64; may be NULL): rows
+ * of each DIC level are then stored in the Morton order of their centres
+ * instead of ascending cell index.  Only the storage order changes; every
+ * result is bit-identical, but the gathers of neighbouring values become
+ * local on meshes whose numbering is not (e.g. randomly renumbered ones). */
+spuma_status spuma_ldu_create_with_centres(int32_t n_cells, int32_t n_faces, const int32_t* lower_addr,
+                                           const int32_t* upper_addr, const double* cell_c,
+                                           void* workspace, size_t workspace_bytes,
+                                           spuma_stream_t stream, spuma_ldu_t* out);
 spuma_status spuma_ldu_destroy(spuma_ldu_t h);
 /* Host-side facts of a handle: cell and face count, DIC level count. */
 spuma_status spuma_ldu_info(spuma_ldu_t h, int32_t* n_cells, int32_t* n_faces, int32_t* n_levels);
@@ -267,6 +276,15 @@ int32_t spuma_tune_cache_store(const char* path, const char* signature, int32_t 
  * sets it to 0 to check that an expired wait returns
  * SPUMA_ERR_DEVICE_TIMEOUT instead of hanging.
  * ---------------------------------------------------------------------- */
+/* spuma_read_phase_clocks: when the environment variable SPUMA_PHASE_CLOCKS
+ * is set at launch, the solver's first block adds SM-clock cycles per phase
+ * into a table in the workspace (slots 0..63 forward DIC level L, 64..127
+ * backward level L, 128 search direction, 129 Amul + p.Ap, 130 diagonal
+ * pass, 131 initial residual, 132 FP64 refinement residual, 133 inner
+ * start, 134 correction, 140 PCG iterations); this copies the first n
+ * entries (synchronous).  SPUMA_ROW_MODE=1 selects the warp-cooperative row
+ * kernels, SPUMA_SOLVE_BLOCKS_PER_SM caps the solver's blocks per SM.      */
+spuma_status spuma_read_phase_clocks(spuma_ldu_t h, int64_t* out, int32_t n, spuma_stream_t stream);
 const char* spuma_status_string(int32_t status);
 const char* spuma_last_error(void);
 uint64_t spuma_launch_count(void);

@@ -50,6 +50,7 @@ _H = C.c_void_p
 _SIGS = {
     "spuma_workspace_bytes": (C.c_size_t, [_I, _I, _I]),
     "spuma_ldu_create": (_I, [_I, _I, _P, _P, _P, C.c_size_t, _P, C.POINTER(_H)]),
+    "spuma_ldu_create_with_centres": (_I, [_I, _I, _P, _P, _P, _P, C.c_size_t, _P, C.POINTER(_H)]),
     "spuma_ldu_destroy": (_I, [_H]),
     "spuma_ldu_info": (_I, [_H, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "spuma_ldu_device_status": (_I, [_H, _P]),
@@ -73,6 +74,7 @@ _SIGS = {
     "spuma_tune_cache_lookup": (_I, [C.c_char_p, C.c_char_p, C.POINTER(_I), C.POINTER(_I),
                                      C.POINTER(C.c_double)]),
     "spuma_tune_cache_store": (_I, [C.c_char_p, C.c_char_p, _I, _I, C.c_double]),
+    "spuma_read_phase_clocks": (_I, [_H, C.POINTER(C.c_int64), _I, _P]),
     "spuma_status_string": (C.c_char_p, [_I]),
     "spuma_last_error": (C.c_char_p, []),
     "spuma_launch_count": (C.c_uint64, []),

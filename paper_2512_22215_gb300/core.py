@@ -44,7 +44,7 @@ def read_perf(t: torch.Tensor) -> list[dict]:
 class LduMesh:
     """A mesh's LDU addressing on the device plus the library workspace."""
 
-    def __init__(self, lower, upper_addr, n_cells: int, device="cuda"):
+    def __init__(self, lower, upper_addr, n_cells: int, device="cuda", centres=None):
         L = lib()
         dev = torch.device(device)
         lower = torch.as_tensor(lower, dtype=torch.int32).to(dev).contiguous()
@@ -58,8 +58,11 @@ class LduMesh:
         base = self.workspace.data_ptr()
         self._ws_ptr = (base + 255) // 256 * 256
         h = C.c_void_p()
-        st = L.spuma_ldu_create(self.n_cells, self.n_faces, ptr(lower), ptr(upper_addr), self._ws_ptr, nbytes,
-                                stream_ptr(), C.byref(h))
+        cc = None
+        if centres is not None:
+            cc = torch.as_tensor(centres, dtype=torch.float64).to(dev).contiguous()
+        st = L.spuma_ldu_create_with_centres(self.n_cells, self.n_faces, ptr(lower), ptr(upper_addr), ptr(cc),
+                                             self._ws_ptr, nbytes, stream_ptr(), C.byref(h))
         check(st, "spuma_ldu_create")
         self.handle = h
         self.lower = lower

@@ -224,15 +224,26 @@ spuma_status spuma_batch_create(int32_t n_sys, const spuma_ldu_t* hs, const doub
         a.b_orig = b[k];
         a.x_orig = x[k];
         a.perf = perf + k;
-        cudaError_t e = cudaMemcpyAsync(hs[k]->at<SolveArgs>(hs[k]->L.args), &a, sizeof(SolveArgs),
-                                        cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemcpyAsync(args)"));
         hs[k]->prepared_precond = ctl->precond;
     }
+    // trial runs of the tuner start from 0 and leave the caller's x alone
+    spuma_status st;
+    auto upload = [&](bool trial) -> spuma_status {
+        for (int k = 0; k < n_sys; k++) {
+            SolveArgs a = bt->args[k];
+            if (trial) {
+                a.zero_x0 = 1;
+                a.no_store = 1;
+            }
+            SPUMA_CUDA(cudaMemcpyAsync(hs[k]->at<SolveArgs>(hs[k]->L.args), &a, sizeof(SolveArgs),
+                                       cudaMemcpyHostToDevice, s));
+        }
+        return cudaStreamSynchronize(s) == cudaSuccess ? SPUMA_OK : cuda_fail(cudaGetLastError(), "args upload");
+    };
     int num_sms = hs[0]->num_sms;
     int threads = ctl->block_threads > 0 ? ctl->block_threads : 256, policy = 1;
-    spuma_status st;
     if (autotune) {
+        if ((st = upload(true)) != SPUMA_OK) return fail(st);
         const char* path = getenv("SPUMA_TUNE_CACHE");
         std::string sig = batch_signature(bt, ctl, num_sms);
         double ms = 0;
@@ -244,8 +255,8 @@ spuma_status spuma_batch_create(int32_t n_sys, const spuma_ldu_t* hs, const doub
                 return fail(cuda_fail(cudaGetLastError(), "cudaEventCreate"));
             double best = 1e30;
             int bt_t = threads, bt_p = policy;
-            const int cand_t[3] = {128, 256, 512};
-            for (int ti = 0; ti < 3; ti++) {
+            const int cand_t[2] = {128, 256};
+            for (int ti = 0; ti < 2; ti++) {
                 for (int pol = 0; pol < 2; pol++) {
                     if (batch_configure(bt, cand_t[ti], pol, num_sms) != SPUMA_OK) continue;
                     if ((st = batch_launch(bt, s)) != SPUMA_OK) return fail(st);   // warm-up
@@ -274,6 +285,7 @@ spuma_status spuma_batch_create(int32_t n_sys, const spuma_ldu_t* hs, const doub
         }
     }
     if ((st = batch_configure(bt, threads, policy, num_sms)) != SPUMA_OK) return fail(st);
+    if ((st = upload(false)) != SPUMA_OK) return fail(st);
     // capture one launch (barrier resets + the persistent kernel) in a graph
     cudaStream_t cs;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess)

@@ -229,7 +229,7 @@ struct Layout {
     size_t x64, r64, w64, p64, q64, b64;
     size_t x32, r32, w32, p32, q32;
     // control
-    size_t partials, bar, status, args;
+    size_t partials, bar, status, args, clk;
 };
 
 Layout make_layout(int64_t n, int64_t nf);

@@ -8,6 +8,7 @@
 // ("lower") and owner-side ("upper") entries in ascending face order, so each
 // row sum is taken in exactly the order of the sequential face loop.
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <mutex>
 #include <map>
@@ -60,6 +61,163 @@ struct RowIter {
 __device__ __forceinline__ RowIter rows_of(const Group& g)
 {
     return RowIter{g.bid * (int)blockDim.x + (int)threadIdx.x, g.nblocks * (int)blockDim.x};
+}
+
+struct WarpIter {
+    int first, stride, lane;
+};
+
+__device__ __forceinline__ WarpIter warps_of(const Group& g)
+{
+    const int t = g.bid * (int)blockDim.x + (int)threadIdx.x;
+    return WarpIter{t >> 5, (g.nblocks * (int)blockDim.x) >> 5, (int)threadIdx.x & 31};
+}
+
+// Optional phase timing: group block 0, thread 0 adds SM-clock deltas between
+// consecutive marks into phase_clk[slot] (slots: 0..63 forward level, 64..127
+// backward level, 128 search direction, 129 Amul + sigma, 130 diagonal pass,
+// 131 init, 132 outer residual, 133 inner init, 134 correction, 135 gather,
+// 136 factor, 140 iterations).
+enum ClkSlot { CK_FWD = 0, CK_BWD = 64, CK_PUPD = 128, CK_AMUL = 129, CK_DIAG = 130, CK_INIT = 131, CK_RESID = 132,
+               CK_INNER0 = 133, CK_CORR = 134, CK_GATHER = 135, CK_FACTOR = 136, CK_ITERS = 140 };
+__device__ __forceinline__ long long sm_clock()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%clock64;" : "=l"(t));
+    return t;
+}
+
+struct PhaseClock {
+    long long* acc;
+    long long t;
+    __device__ __forceinline__ PhaseClock(long long* a, int bid)
+    {
+        acc = (a && bid == 0 && threadIdx.x == 0) ? a : nullptr;
+        t = sm_clock();
+    }
+    __device__ __forceinline__ void lap(int slot)
+    {
+        if (acc) {
+            const long long now = sm_clock();
+            acc[slot] += now - t;
+            t = now;
+        }
+    }
+    __device__ __forceinline__ void count(int slot)
+    {
+        if (acc) acc[slot] += 1;
+    }
+};
+
+// Per-thread reduction accumulators.  FP64: fused multiply-add into a double.
+// FP32 data: the exact product (a*b, fma(a, b, -a*b)) is added to a
+// double-float (hi, lo) pair by Knuth's two-sum, so the sum keeps ~48 bits
+// without converting every element to double; the pair is converted once.
+template <class T>
+struct Acc;
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void prod(double a, double b) { s = __fma_rn(a, b, s); }
+    __device__ __forceinline__ void add(double a) { s = __dadd_rn(s, a); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct Acc<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add2(float p, float e)
+    {
+        const float sum = __fadd_rn(hi, p);
+        const float bb = __fsub_rn(sum, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(sum, bb)), __fsub_rn(p, bb));
+        hi = sum;
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ void prod(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        add2(p, __fmaf_rn(a, b, -p));
+    }
+    __device__ __forceinline__ void add(float a) { add2(a, 0.0f); }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// Warp-cooperative row chains.  A warp owns 32 consecutive rows whose entries
+// [cb0, ce0) are contiguous; it loads them coalesced, issues every gather of
+// the chunk at once, stages (coefficient, gathered value) pairs in shared
+// memory, and each lane then runs its own row's multiply-add chain in entry
+// order (DESC: descending), exactly as the sequential face loop would.
+constexpr int kSub = 128;        // staged entries per warp and sub-chunk
+constexpr int kMaxWarps = 8;     // 256 threads per block
+__shared__ __align__(16) unsigned char g_stage[kMaxWarps * kSub * 16];
+
+template <class T, bool DESC, bool NEG>
+__device__ __forceinline__ T warp_chain(T acc, int eb, int ee, int cb0, int ce0, const int* col, const T* coef,
+                                        const T* vec, int lane)
+{
+    if (ce0 <= cb0) return acc;
+    T* sc = reinterpret_cast<T*>(g_stage) + (threadIdx.x >> 5) * (2 * kSub);
+    T* sv = sc + kSub;
+    const int nsub = (ce0 - cb0 + kSub - 1) / kSub;
+    for (int si = 0; si < nsub; si++) {
+        const int base = cb0 + (DESC ? nsub - 1 - si : si) * kSub;
+        const int lim = min(ce0, base + kSub);
+        int ci[kSub / 32];
+        T cv[kSub / 32];
+#pragma unroll
+        for (int k = 0; k < kSub / 32; k++) {
+            const int e = base + lane + 32 * k;
+            ci[k] = e < lim ? __ldg(col + e) : -1;
+            cv[k] = e < lim ? coef[e] : T(0);
+        }
+        T gv[kSub / 32];
+#pragma unroll
+        for (int k = 0; k < kSub / 32; k++) gv[k] = ci[k] >= 0 ? vec[ci[k]] : T(0);
+#pragma unroll
+        for (int k = 0; k < kSub / 32; k++) {
+            const int o = lane + 32 * k;
+            if (base + o < lim) {
+                sc[o] = cv[k];
+                sv[o] = gv[k];
+            }
+        }
+        __syncwarp();
+        const int lo = max(eb, base) - base, hi = min(ee, lim) - base;
+        if (DESC) {
+            for (int o = hi - 1; o >= lo; o--) acc = fmadd(NEG ? -sc[o] : sc[o], sv[o], acc);
+        } else {
+            for (int o = lo; o < hi; o++) acc = fmadd(NEG ? -sc[o] : sc[o], sv[o], acc);
+        }
+        __syncwarp();
+    }
+    return acc;
+}
+
+// Entry range of the lane's row and of the warp's chunk of rows [p0, p0+nv).
+__device__ __forceinline__ void chunk_range(const int* ptr, int p0, int nv, int lane, int& eb, int& ee, int& cb0,
+                                            int& ce0)
+{
+    const bool v = lane < nv;
+    eb = v ? __ldg(ptr + p0 + lane) : 0;
+    ee = v ? __ldg(ptr + p0 + lane + 1) : 0;
+    cb0 = __shfl_sync(0xffffffffu, eb, 0);
+    ce0 = __shfl_sync(0xffffffffu, ee, nv - 1);
+}
+
+// y_p = d_p x_p + lower entries (ascending face) + upper entries (ascending
+// face), warp-cooperative; valid lanes return y for row p0 + lane.
+template <class T>
+__device__ __forceinline__ T warp_amul_row(const Mat<T>& A, const T* x, int p0, int nv, int lane)
+{
+    const int p = p0 + lane;
+    const bool v = lane < nv;
+    T y = v ? mul_rn(A.d[p], x[p]) : T(0);
+    int eb, ee, cb0, ce0;
+    chunk_range(A.Lptr, p0, nv, lane, eb, ee, cb0, ce0);
+    y = warp_chain<T, false, false>(y, eb, ee, cb0, ce0, A.Lcol, A.La, x, lane);
+    chunk_range(A.Uptr, p0, nv, lane, eb, ee, cb0, ce0);
+    y = warp_chain<T, false, false>(y, eb, ee, cb0, ce0, A.Ucol, A.Ua, x, lane);
+    return y;
 }
 
 // ------------------------------------------------------------ phases --------
@@ -138,10 +296,78 @@ __device__ bool phase_factor(const SolveArgs& a, const Group& g)
 // x/r update of the previous PCG iteration (x += alpha p, r -= alpha q) and
 // the sum|r| of the updated residual (slot A).
 template <class T>
-__device__ bool dic_forward(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool pending, T alpha, const Group& g)
+__device__ bool dic_forward_warp(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool pending, T alpha, const Group& g,
+                                 PhaseClock& pc)
+{
+    const WarpIter wi = warps_of(g);
+    Acc<T> acc;
+    for (int L = 0; L < a.nlev; L++) {
+        const int r0 = a.lvl[L], r1 = a.lvl[L + 1];
+        for (int p0 = r0 + 32 * wi.first; p0 < r1; p0 += 32 * wi.stride) {
+            const int nv = min(32, r1 - p0), p = p0 + wi.lane;
+            const bool ok = wi.lane < nv;
+            T rr = ok ? v.r[p] : T(0);
+            if (pending && ok) {
+                v.x[p] = fmadd(alpha, v.p[p], v.x[p]);
+                rr = fmadd(-alpha, v.q[p], rr);
+                v.r[p] = rr;
+                acc.add(fabs(rr));
+            }
+            T ww = ok ? mul_rn(A.rD[p], rr) : T(0);
+            int eb, ee, cb0, ce0;
+            chunk_range(A.Lptr, p0, nv, wi.lane, eb, ee, cb0, ce0);
+            ww = warp_chain<T, false, true>(ww, eb, ee, cb0, ce0, A.Lcol, A.Lc, v.w, wi.lane);
+            if (ok) v.w[p] = ww;
+        }
+        if (L == a.nlev - 1 && pending) {
+            double t[1] = {acc.value()};
+            block_reduce_store<1>(t, a.partials, SL_A, g.bid);
+        }
+        if (!group_sync(g)) return false;
+        pc.lap(CK_FWD + min(L, 63));
+    }
+    return true;
+}
+
+// DIC backward sweep (levels descending, upper entries descending face order),
+// with rho = sum w r into slot B.
+template <class T>
+__device__ bool dic_backward_warp(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool want_rho, const Group& g,
+                                  PhaseClock& pc)
+{
+    const WarpIter wi = warps_of(g);
+    Acc<T> acc;
+    for (int L = a.nlev - 1; L >= 0; L--) {
+        const int r0 = a.lvl[L], r1 = a.lvl[L + 1];
+        for (int p0 = r0 + 32 * wi.first; p0 < r1; p0 += 32 * wi.stride) {
+            const int nv = min(32, r1 - p0), p = p0 + wi.lane;
+            const bool ok = wi.lane < nv;
+            T ww = ok ? v.w[p] : T(0);
+            int eb, ee, cb0, ce0;
+            chunk_range(A.Uptr, p0, nv, wi.lane, eb, ee, cb0, ce0);
+            ww = warp_chain<T, true, true>(ww, eb, ee, cb0, ce0, A.Ucol, A.Uc, v.w, wi.lane);
+            if (ok) {
+                v.w[p] = ww;
+                acc.prod(ww, v.r[p]);
+            }
+        }
+        if (L == 0 && want_rho) {
+            double t[1] = {acc.value()};
+            block_reduce_store<1>(t, a.partials, SL_B, g.bid);
+        }
+        if (!group_sync(g)) return false;
+        pc.lap(CK_BWD + min(L, 63));
+    }
+    return true;
+}
+
+// One thread per row variants of the two sweeps.
+template <class T>
+__device__ bool dic_forward_thread(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool pending, T alpha,
+                                   const Group& g, PhaseClock& pc)
 {
     RowIter it = rows_of(g);
-    double acc = 0.0;
+    Acc<T> acc;
     for (int L = 0; L < a.nlev; L++) {
         const int r0 = a.lvl[L], r1 = a.lvl[L + 1];
         for (int p = r0 + it.first; p < r1; p += it.stride) {
@@ -150,53 +376,73 @@ __device__ bool dic_forward(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool
                 v.x[p] = fmadd(alpha, v.p[p], v.x[p]);
                 rr = fmadd(-alpha, v.q[p], rr);
                 v.r[p] = rr;
-                acc += fabs((double)rr);
+                acc.add(fabs(rr));
             }
             T ww = mul_rn(A.rD[p], rr);
-            for (int e = A.Lptr[p]; e < A.Lptr[p + 1]; e++) ww = fmadd(-A.Lc[e], v.w[A.Lcol[e]], ww);
+            const int e1 = A.Lptr[p + 1];
+            for (int e = A.Lptr[p]; e < e1; e++) ww = fmadd(-A.Lc[e], v.w[A.Lcol[e]], ww);
             v.w[p] = ww;
         }
         if (L == a.nlev - 1 && pending) {
-            double t[1] = {acc};
+            double t[1] = {acc.value()};
             block_reduce_store<1>(t, a.partials, SL_A, g.bid);
         }
         if (!group_sync(g)) return false;
+        pc.lap(CK_FWD + min(L, 63));
     }
     return true;
 }
 
-// DIC backward sweep (levels descending, upper entries descending face order),
-// with rho = sum w r into slot B.
 template <class T>
-__device__ bool dic_backward(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool want_rho, const Group& g)
+__device__ bool dic_backward_thread(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool want_rho, const Group& g,
+                                    PhaseClock& pc)
 {
     RowIter it = rows_of(g);
-    double acc = 0.0;
+    Acc<T> acc;
     for (int L = a.nlev - 1; L >= 0; L--) {
         const int r0 = a.lvl[L], r1 = a.lvl[L + 1];
         for (int p = r0 + it.first; p < r1; p += it.stride) {
             T ww = v.w[p];
-            for (int e = A.Uptr[p + 1] - 1; e >= A.Uptr[p]; e--) ww = fmadd(-A.Uc[e], v.w[A.Ucol[e]], ww);
+            const int e0 = A.Uptr[p];
+            for (int e = A.Uptr[p + 1] - 1; e >= e0; e--) ww = fmadd(-A.Uc[e], v.w[A.Ucol[e]], ww);
             v.w[p] = ww;
-            acc = fma((double)ww, (double)v.r[p], acc);
+            acc.prod(ww, v.r[p]);
         }
         if (L == 0 && want_rho) {
-            double t[1] = {acc};
+            double t[1] = {acc.value()};
             block_reduce_store<1>(t, a.partials, SL_B, g.bid);
         }
         if (!group_sync(g)) return false;
+        pc.lap(CK_BWD + min(L, 63));
     }
     return true;
 }
 
+template <class T, int RM>
+__device__ __forceinline__ bool dic_forward(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool pending, T alpha,
+                                            const Group& g, PhaseClock& pc)
+{
+    if (RM) return dic_forward_warp<T>(a, A, v, pending, alpha, g, pc);
+    return dic_forward_thread<T>(a, A, v, pending, alpha, g, pc);
+}
+
+template <class T, int RM>
+__device__ __forceinline__ bool dic_backward(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool want_rho,
+                                             const Group& g, PhaseClock& pc)
+{
+    if (RM) return dic_backward_warp<T>(a, A, v, want_rho, g, pc);
+    return dic_backward_thread<T>(a, A, v, want_rho, g, pc);
+}
+
 // PCG iterations on (A, v.r) from the current v.x (OpenFOAM recurrences).
 // Returns the iteration count, or -1 when a device error stopped the group.
-template <class T>
+template <class T, int RM>
 __device__ int pcg_loop(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, double nfac, double res0, double tol,
                         double rel_tol, int max_iter, int min_iter, double* res_out, int* singular,
                         const Group& g)
 {
     RowIter it = rows_of(g);
+    PhaseClock pc(a.phase_clk, g.bid);
     double res = res0;
     *res_out = res;
     if (!(min_iter > 0 || !converged(res0, res0, tol, rel_tol))) return 0;
@@ -207,7 +453,7 @@ __device__ int pcg_loop(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, double n
     for (;;) {
         rho_old = rho;
         if (a.precond == SPUMA_PRECOND_DIC) {
-            if (!dic_forward<T>(a, A, v, pending, alpha, g)) return -1;
+            if (!dic_forward<T, RM>(a, A, v, pending, alpha, g, pc)) return -1;
             if (pending) {
                 double t[1];
                 grid_reduce_read<1>(t, a.partials, SL_A, g.nblocks);
@@ -215,26 +461,28 @@ __device__ int pcg_loop(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, double n
                 n_it++;
                 if (!((n_it < max_iter && !converged(res, res0, tol, rel_tol)) || n_it < min_iter)) break;
             }
-            if (!dic_backward<T>(a, A, v, true, g)) return -1;
+            if (!dic_backward<T, RM>(a, A, v, true, g, pc)) return -1;
             double t[1];
             grid_reduce_read<1>(t, a.partials, SL_B, g.nblocks);
             rho = t[0];
         } else {
-            double acc[2] = {0.0, 0.0};
+            Acc<T> ares, arho;
             for (int p = it.first; p < a.n; p += it.stride) {
                 T rr = v.r[p];
                 if (pending) {
                     v.x[p] = fmadd(alpha, v.p[p], v.x[p]);
                     rr = fmadd(-alpha, v.q[p], rr);
                     v.r[p] = rr;
-                    acc[0] += fabs((double)rr);
+                    ares.add(fabs(rr));
                 }
                 T ww = a.precond == SPUMA_PRECOND_DIAGONAL ? mul_rn(A.rD[p], rr) : rr;
                 v.w[p] = ww;
-                acc[1] = fma((double)ww, (double)rr, acc[1]);
+                arho.prod(ww, rr);
             }
+            double acc[2] = {ares.value(), arho.value()};
             block_reduce_store<2>(acc, a.partials, SL_A, g.bid);
             if (!group_sync(g)) return -1;
+            pc.lap(CK_DIAG);
             double t[2];
             grid_reduce_read<2>(t, a.partials, SL_A, g.nblocks);
             if (pending) {
@@ -249,15 +497,31 @@ __device__ int pcg_loop(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, double n
         const T beta = first ? (T)0 : (T)(rho / rho_old);
         for (int p = it.first; p < a.n; p += it.stride) v.p[p] = first ? v.w[p] : fmadd(beta, v.p[p], v.w[p]);
         if (!group_sync(g)) return -1;
+        pc.lap(CK_PUPD);
         // q = A p, sigma = q.p
-        double sacc[1] = {0.0};
-        for (int p = it.first; p < a.n; p += it.stride) {
-            T qq = amul_row<T>(A, v.p, p);
-            v.q[p] = qq;
-            sacc[0] = fma((double)qq, (double)v.p[p], sacc[0]);
+        Acc<T> asig;
+        if (RM) {
+            const WarpIter wi = warps_of(g);
+            for (int p0 = 32 * wi.first; p0 < a.n; p0 += 32 * wi.stride) {
+                const int nv = min(32, a.n - p0), p = p0 + wi.lane;
+                const T qq = warp_amul_row<T>(A, v.p, p0, nv, wi.lane);
+                if (wi.lane < nv) {
+                    v.q[p] = qq;
+                    asig.prod(qq, v.p[p]);
+                }
+            }
+        } else {
+            for (int p = it.first; p < a.n; p += it.stride) {
+                const T qq = amul_row<T>(A, v.p, p);
+                v.q[p] = qq;
+                asig.prod(qq, v.p[p]);
+            }
         }
+        double sacc[1] = {asig.value()};
         block_reduce_store<1>(sacc, a.partials, SL_C, g.bid);
         if (!group_sync(g)) return -1;
+        pc.lap(CK_AMUL);
+        pc.count(CK_ITERS);
         double sg[1];
         grid_reduce_read<1>(sg, a.partials, SL_C, g.nblocks);
         if (fabs(sg[0]) / nfac < 1e-300) {
@@ -324,6 +588,7 @@ __device__ void phase_store_x(const SolveArgs& a, const Group& g)
 }
 
 // Mixed precision: FP64 refinement around FP32 inner PCG.
+template <int RM>
 __device__ bool solve_mixed(const SolveArgs& a, const Group& g, double nfac, spuma_solver_perf& pf)
 {
     RowIter it = rows_of(g);
@@ -334,11 +599,25 @@ __device__ bool solve_mixed(const SolveArgs& a, const Group& g, double nfac, spu
     double res = 0.0, res0 = 0.0;
     for (;;) {
         double acc[1] = {0.0}, mx[1] = {0.0};
-        for (int p = it.first; p < a.n; p += it.stride) {
-            double rr = a.b[p] - amul_row<double>(A64, a.x, p);
-            a.r[p] = rr;
-            acc[0] += fabs(rr);
-            mx[0] = fmax(mx[0], fabs(rr));
+        if (!RM) {
+            for (int p = it.first; p < a.n; p += it.stride) {
+                const double rr = a.b[p] - amul_row<double>(A64, a.x, p);
+                a.r[p] = rr;
+                acc[0] += fabs(rr);
+                mx[0] = fmax(mx[0], fabs(rr));
+            }
+        } else {
+            const WarpIter wi = warps_of(g);
+            for (int p0 = 32 * wi.first; p0 < a.n; p0 += 32 * wi.stride) {
+                const int nv = min(32, a.n - p0), p = p0 + wi.lane;
+                const double ax = warp_amul_row<double>(A64, a.x, p0, nv, wi.lane);
+                if (wi.lane < nv) {
+                    const double rr = a.b[p] - ax;
+                    a.r[p] = rr;
+                    acc[0] += fabs(rr);
+                    mx[0] = fmax(mx[0], fabs(rr));
+                }
+            }
         }
         block_reduce_store<1>(acc, a.partials, SL_A, g.bid);
         block_max_store<1>(mx, a.partials, SL_B, g.bid);
@@ -351,13 +630,14 @@ __device__ bool solve_mixed(const SolveArgs& a, const Group& g, double nfac, spu
         if (res < a.tol || outer >= a.max_outer || singular) break;
         const double s = m[0];
         if (s == 0.0) break;
-        double iacc[1] = {0.0};
+        Acc<float> ain;
         for (int p = it.first; p < a.n; p += it.stride) {
             float rv = (float)(a.r[p] / s);
             vi.r[p] = rv;
             vi.x[p] = 0.0f;
-            iacc[0] += fabs((double)rv);
+            ain.add(fabsf(rv));
         }
+        double iacc[1] = {ain.value()};
         block_reduce_store<1>(iacc, a.partials, SL_C, g.bid);
         if (!group_sync(g)) return false;
         double ti[1];
@@ -365,7 +645,7 @@ __device__ bool solve_mixed(const SolveArgs& a, const Group& g, double nfac, spu
         const double infac = ti[0] + 1e-20;
         const double ires0 = ti[0] / infac;
         double ires;
-        int n_in = pcg_loop<float>(a, A32, vi, infac, ires0, 0.0, a.inner_rel_tol, a.max_iter, 1, &ires, &singular, g);
+        int n_in = pcg_loop<float, RM>(a, A32, vi, infac, ires0, 0.0, a.inner_rel_tol, a.max_iter, 1, &ires, &singular, g);
         if (n_in < 0) return false;
         total += n_in;
         for (int p = it.first; p < a.n; p += it.stride) a.x[p] = fma(s, (double)vi.x[p], a.x[p]);
@@ -381,6 +661,7 @@ __device__ bool solve_mixed(const SolveArgs& a, const Group& g, double nfac, spu
     return true;
 }
 
+template <int RM>
 __device__ void run_system(const SolveArgs& a, const Group& g)
 {
     spuma_solver_perf pf;
@@ -406,8 +687,9 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
         const Mat<double> A = mat_of<double>(a);
         if (ok) {
             if (a.precond == SPUMA_PRECOND_DIC) {
-                ok = dic_forward<double>(a, A, v, false, 0.0, g);
-                if (ok) ok = dic_backward<double>(a, A, v, false, g);
+                PhaseClock pc(nullptr, g.bid);
+                ok = dic_forward<double, RM>(a, A, v, false, 0.0, g, pc);
+                if (ok) ok = dic_backward<double, RM>(a, A, v, false, g, pc);
             } else {
                 for (int p = it.first; p < a.n; p += it.stride)
                     a.w[p] = a.precond == SPUMA_PRECOND_DIAGONAL ? __dmul_rn(a.rD64[p], a.r[p]) : a.r[p];
@@ -422,12 +704,12 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
         ok = phase_init(a, g, &nfac, &res0);
         if (ok) {
             if (a.precision == SPUMA_MIXED) {
-                ok = solve_mixed(a, g, nfac, pf);
+                ok = solve_mixed<RM>(a, g, nfac, pf);
             } else {
                 Vecs<double> v{a.x, a.r, a.w, a.p, a.q};
                 double res;
                 int sing = 0;
-                int n_it = pcg_loop<double>(a, mat_of<double>(a), v, nfac, res0, a.tol, a.rel_tol, a.max_iter,
+                int n_it = pcg_loop<double, RM>(a, mat_of<double>(a), v, nfac, res0, a.tol, a.rel_tol, a.max_iter,
                                             a.min_iter, &res, &sing, g);
                 ok = n_it >= 0;
                 pf.initial_residual = res0;
@@ -437,7 +719,7 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
                 pf.singular = sing;
             }
         }
-        if (ok) phase_store_x(a, g);
+        if (ok && !a.no_store) phase_store_x(a, g);
     }
     if (g.bid == 0 && threadIdx.x == 0 && a.perf) {
         __threadfence();
@@ -447,13 +729,14 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
     }
 }
 
-__global__ void __launch_bounds__(512) k_solve(SolveArgs a, unsigned long long timeout_ns)
+template <int RM>
+__global__ void __launch_bounds__(256, RM ? 3 : 4) k_solve(SolveArgs a, unsigned long long timeout_ns)
 {
     Group g{a.bar, a.bar + 32, a.status, (int)gridDim.x, (int)blockIdx.x, timeout_ns};
-    run_system(a, g);
+    run_system<RM>(a, g);
 }
 
-__global__ void __launch_bounds__(512) k_solve_batch(BatchTable t, unsigned long long timeout_ns)
+__global__ void __launch_bounds__(256, 3) k_solve_batch(BatchTable t, unsigned long long timeout_ns)
 {
     __shared__ SolveArgs sa;
     int s = 0;
@@ -461,14 +744,27 @@ __global__ void __launch_bounds__(512) k_solve_batch(BatchTable t, unsigned long
     if (threadIdx.x == 0) sa = *t.args[s];
     __syncthreads();
     Group g{sa.bar, sa.bar + 32, sa.status, t.split[s + 1] - t.split[s], (int)blockIdx.x - t.split[s], timeout_ns};
-    run_system(sa, g);
+    run_system<0>(sa, g);
 }
 
 // Stand-alone Amul on the prepared matrix (internal order).
 template <class T>
-__global__ void k_amul_prepared(int n, Mat<T> A, const T* __restrict__ x, T* __restrict__ y)
+__global__ void __launch_bounds__(256) k_amul_prepared_thread(int n, Mat<T> A, const T* __restrict__ x,
+                                                              T* __restrict__ y)
 {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) y[p] = amul_row<T>(A, x, p);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_amul_prepared(int n, Mat<T> A, const T* __restrict__ x, T* __restrict__ y)
+{
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int p0 = 32 * w0; p0 < n; p0 += 32 * nw) {
+        const int nv = min(32, n - p0);
+        const T yy = warp_amul_row<T>(A, x, p0, nv, lane);
+        if (lane < nv) y[p0 + lane] = yy;
+    }
 }
 
 __global__ void k_permute(int n, int dir, const int* __restrict__ perm, const double* __restrict__ src, double* dst)
@@ -531,18 +827,30 @@ SolveArgs make_args(spuma_ldu_t h)
     return a;
 }
 
+// Row-processing variant of the persistent solver (SPUMA_ROW_MODE=1 selects
+// the warp-cooperative chunks; default one thread per row).
+static int row_mode()
+{
+    static int m = [] {
+        const char* e = getenv("SPUMA_ROW_MODE");
+        return e && atoi(e) == 1 ? 1 : 0;
+    }();
+    return m;
+}
+
 static std::mutex g_occ_mu;
 static std::map<int, int> g_occ;   // (kernel, block threads) -> co-resident blocks per SM
 
 int solve_blocks_per_sm(int threads, bool batch)
 {
     std::lock_guard<std::mutex> lk(g_occ_mu);
-    const int key = threads * 2 + (batch ? 1 : 0);
+    const int key = threads * 4 + (batch ? 2 : 0) + row_mode();
     auto it = g_occ.find(key);
     if (it != g_occ.end()) return it->second;
     int nb = 0;
     cudaError_t e = batch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve_batch, threads, 0)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve, threads, 0);
+                          : (row_mode() ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<1>, threads, 0)
+                                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<0>, threads, 0));
     if (e != cudaSuccess) nb = 0;
     g_occ[key] = nb;
     return nb;
@@ -556,19 +864,32 @@ int default_threads(const spuma_solver_controls* ctl)
 
 spuma_status launch_solve(spuma_ldu_t h, const SolveArgs& a, int threads, cudaStream_t s)
 {
-    if (threads < 32 || threads > 1024 || threads % 32) {
-        set_error("block_threads must be a multiple of 32 in [32, 1024]");
+    if (threads < 32 || threads > 256 || threads % 32) {
+        set_error("block_threads must be a multiple of 32 in [32, 256]");
         return SPUMA_ERR_INVALID_ARG;
     }
     int per_sm = solve_blocks_per_sm(threads, false);
     if (per_sm < 1) { set_error("solver kernel cannot be resident"); return SPUMA_ERR_CUDA; }
+    // SPUMA_SOLVE_BLOCKS_PER_SM caps the co-resident blocks per SM used by the
+    // persistent solver (a tuning override; default: all that fit)
+    if (const char* env = getenv("SPUMA_SOLVE_BLOCKS_PER_SM")) {
+        int v = atoi(env);
+        if (v >= 1 && v < per_sm) per_sm = v;
+    }
     int64_t want = ((int64_t)a.n + threads - 1) / threads;
     int64_t maxg = std::min<int64_t>((int64_t)per_sm * h->num_sms, kMaxBlocks);
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, maxg));
     SPUMA_CUDA(cudaMemsetAsync(h->at<char>(h->L.bar), 0, h->L.status + 256 - h->L.bar, s));
     unsigned long long tns = barrier_timeout_ns();
-    void* args[] = {(void*)&a, (void*)&tns};
-    SPUMA_CUDA(cudaLaunchCooperativeKernel((const void*)k_solve, grid, threads, args, 0, s));
+    SolveArgs b = a;
+    b.row_mode = row_mode();
+    if (getenv("SPUMA_PHASE_CLOCKS")) {
+        b.phase_clk = h->at<long long>(h->L.clk);
+        SPUMA_CUDA(cudaMemsetAsync(b.phase_clk, 0, 8 * 256, s));
+    }
+    void* args[] = {(void*)&b, (void*)&tns};
+    const void* fn = b.row_mode ? (const void*)k_solve<1> : (const void*)k_solve<0>;
+    SPUMA_CUDA(cudaLaunchCooperativeKernel(fn, grid, threads, args, 0, s));
     count_launch();
     return SPUMA_OK;
 }
@@ -688,10 +1009,16 @@ spuma_status spuma_amul_prepared(spuma_ldu_t h, int32_t precision, const void* x
     cudaStream_t s = (cudaStream_t)stream;
     if (precision == SPUMA_F64) {
         Mat<double> A{a.Lptr, a.Lcol, a.La64, a.Lc64, a.Uptr, a.Ucol, a.Ua64, a.Uc64, a.d64, a.rD64};
-        k_amul_prepared<double><<<g, 256, 0, s>>>(h->n, A, (const double*)x, (double*)y);
+        if (row_mode())
+            k_amul_prepared<double><<<g, 256, 0, s>>>(h->n, A, (const double*)x, (double*)y);
+        else
+            k_amul_prepared_thread<double><<<g, 256, 0, s>>>(h->n, A, (const double*)x, (double*)y);
     } else {
         Mat<float> A{a.Lptr, a.Lcol, a.La32, a.Lc32, a.Uptr, a.Ucol, a.Ua32, a.Uc32, a.d32, a.rD32};
-        k_amul_prepared<float><<<g, 256, 0, s>>>(h->n, A, (const float*)x, (float*)y);
+        if (row_mode())
+            k_amul_prepared<float><<<g, 256, 0, s>>>(h->n, A, (const float*)x, (float*)y);
+        else
+            k_amul_prepared_thread<float><<<g, 256, 0, s>>>(h->n, A, (const float*)x, (float*)y);
     }
     count_launch();
     SPUMA_CUDA(cudaGetLastError());
@@ -729,6 +1056,15 @@ spuma_status spuma_precondition(spuma_ldu_t h, int32_t precond, const double* r,
     a.b_orig = r;
     a.x_orig = w;
     return launch_solve(h, a, 256, (cudaStream_t)stream);
+}
+
+spuma_status spuma_read_phase_clocks(spuma_ldu_t h, int64_t* out, int32_t n, spuma_stream_t stream)
+{
+    if (!h || !out || n < 0 || n > 256) { set_error("spuma_read_phase_clocks: bad argument"); return SPUMA_ERR_INVALID_ARG; }
+    SPUMA_CUDA(cudaMemcpyAsync(out, h->at<long long>(h->L.clk), 8 * (size_t)n, cudaMemcpyDeviceToHost,
+                               (cudaStream_t)stream));
+    SPUMA_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    return SPUMA_OK;
 }
 
 spuma_status spuma_pcg_solve(spuma_ldu_t h, const double* diag, const double* upper, const double* b, double* x,

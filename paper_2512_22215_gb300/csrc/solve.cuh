@@ -13,6 +13,8 @@ struct SolveArgs {
     int precond;           // spuma_precond
     int precision;         // spuma_precision (F64 or MIXED)
     int zero_x0;           // start from x = 0 instead of reading x_orig
+    int no_store;          // leave x_orig untouched (autotuner trial runs)
+    int row_mode;          // 0: one thread per row, 1: warp-cooperative chunks of 32 rows
     int max_iter, min_iter, max_outer;
     double tol, rel_tol, inner_rel_tol;
     const int* lvl;        // [nlev+1] level starts (internal order)
@@ -34,6 +36,7 @@ struct SolveArgs {
     unsigned* bar;
     int* status;
     spuma_solver_perf* perf;
+    long long* phase_clk;  // optional per-phase SM-clock totals of group block 0 (diagnostics)
 };
 
 struct BatchTable {

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 
 #include "common.cuh"
@@ -81,6 +82,7 @@ Layout make_layout(int64_t n, int64_t nf)
     L.bar = take(1024);
     L.status = take(256);
     L.args = take(4096);
+    L.clk = take(8 * 256);
     L.bytes = off;
     return L;
 }
@@ -270,19 +272,26 @@ __global__ void k_max_level(int n, const int* __restrict__ level, int* st)
     if ((threadIdx.x & 31) == 0) atomicMax(st + DS_MAXLEVEL, m);
 }
 
-// Stable partition of the rows by level: warp k owns rows [k*C, (k+1)*C).
-__global__ void k_level_count(int n, int chunk, int nchunks, const int* __restrict__ level, int* table)
+// Stable partition by bucket: positions 0..n-1 visit the items order[pos]
+// (or pos when order is NULL); warp k owns positions [k*C, (k+1)*C).  Used
+// for the partition of the rows by DIC level and for the passes of the radix
+// sort of the cells by locality key.
+__global__ void k_bucket_count(int n, int chunk, int nchunks, const int* __restrict__ order,
+                               const int* __restrict__ bucket, int* table)
 {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int k = warp; k < nchunks; k += nwarps) {
         int i0 = k * chunk, i1 = min(n, i0 + chunk);
-        for (int i = i0 + lane; i < i1; i += 32) atomicAdd(table + (size_t)level[i] * nchunks + k, 1);
+        for (int i = i0 + lane; i < i1; i += 32) {
+            const int item = order ? order[i] : i;
+            atomicAdd(table + (size_t)bucket[item] * nchunks + k, 1);
+        }
     }
 }
 
-__global__ void k_level_scatter(int n, int chunk, int nchunks, const int* __restrict__ level, int* table,
-                                int* perm, int* iperm)
+__global__ void k_bucket_scatter(int n, int chunk, int nchunks, const int* __restrict__ order,
+                                 const int* __restrict__ bucket, int* table, int* out_order, int* out_pos)
 {
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -292,22 +301,97 @@ __global__ void k_level_scatter(int n, int chunk, int nchunks, const int* __rest
         for (int ib = i0; ib < i1; ib += 32) {
             int i = ib + lane;
             bool act = i < i1;
+            const int item = act ? (order ? order[i] : i) : 0;
+            int bk = act ? bucket[item] : -1;
             unsigned am = __ballot_sync(0xffffffffu, act);
-            int lv = act ? level[i] : -1;
-            unsigned peers = __match_any_sync(0xffffffffu, lv);
+            unsigned peers = __match_any_sync(0xffffffffu, bk);
             int base = 0;
-            size_t slot = (size_t)(act ? lv : 0) * nchunks + k;
+            size_t slot = (size_t)(act ? bk : 0) * nchunks + k;
             if (act) base = table[slot];
             __syncwarp();
             if (act) {
                 int pos = base + __popc(peers & lt & am);
-                perm[pos] = i;
-                iperm[i] = pos;
+                out_order[pos] = item;
+                if (out_pos) out_pos[item] = pos;
                 if ((peers & lt & am) == 0) table[slot] = base + __popc(peers & am);
             }
             __syncwarp();
         }
     }
+}
+
+// Locality key of each cell: a 30-bit Morton code of its centre in the
+// bounding box of all centres (10 bits per axis).
+__global__ void k_bbox_partial(int n, const double* __restrict__ c, double* part)
+{
+    __shared__ double sm[6][32];
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int d = 0; d < 3; d++) {
+            const double v = c[3 * (size_t)i + d];
+            mn[d] = fmin(mn[d], v);
+            mx[d] = fmax(mx[d], v);
+        }
+    for (int d = 0; d < 3; d++)
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[d] = fmin(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+            mx[d] = fmax(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+        }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int d = 0; d < 3; d++) {
+            sm[d][w] = mn[d];
+            sm[3 + d][w] = mx[d];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int d = 0; d < 3; d++) {
+            double a = 1e300, b = -1e300;
+            for (int k = 0; k < nw; k++) {
+                a = fmin(a, sm[d][k]);
+                b = fmax(b, sm[3 + d][k]);
+            }
+            part[6 * blockIdx.x + d] = a;
+            part[6 * blockIdx.x + 3 + d] = b;
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned spread3(unsigned v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__global__ void k_morton(int n, int nparts, const double* __restrict__ c, const double* __restrict__ part,
+                         unsigned* key)
+{
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+    for (int k = 0; k < nparts; k++)
+        for (int d = 0; d < 3; d++) {
+            mn[d] = fmin(mn[d], part[6 * k + d]);
+            mx[d] = fmax(mx[d], part[6 * k + 3 + d]);
+        }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        unsigned q[3];
+        for (int d = 0; d < 3; d++) {
+            const double ext = mx[d] - mn[d];
+            double t = ext > 0.0 ? (c[3 * (size_t)i + d] - mn[d]) / ext : 0.0;
+            int qi = (int)(t * 1024.0);
+            q[d] = (unsigned)min(1023, max(0, qi));
+        }
+        key[i] = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+    }
+}
+
+__global__ void k_digit(int n, const unsigned* __restrict__ key, int shift, int* digit)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        digit[i] = (int)((key[i] >> shift) & 255u);
 }
 
 __global__ void k_level_starts(int nlev, int nchunks, const int* __restrict__ table, int n, int* lvl)
@@ -395,6 +479,13 @@ size_t spuma_workspace_bytes(int32_t n_cells, int32_t n_faces, int32_t flags)
 
 spuma_status spuma_ldu_create(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, void* workspace,
                               size_t workspace_bytes, spuma_stream_t stream, spuma_ldu_t* out)
+{
+    return spuma_ldu_create_with_centres(n, nf, l, u, nullptr, workspace, workspace_bytes, stream, out);
+}
+
+spuma_status spuma_ldu_create_with_centres(int32_t n, int32_t nf, const int32_t* l, const int32_t* u,
+                                           const double* cell_c, void* workspace, size_t workspace_bytes,
+                                           spuma_stream_t stream, spuma_ldu_t* out)
 {
     if (!out) { set_error("out is NULL"); return SPUMA_ERR_INVALID_ARG; }
     *out = nullptr;
@@ -487,30 +578,63 @@ spuma_status spuma_ldu_create(int32_t n, int32_t nf, const int32_t* l, const int
         CU(cudaStreamSynchronize(s));
         nlev = hmax + 1;
 
-        // stable partition by level; the count table and its scan temporaries
-        // use the matrix region (48F + 24N bytes, not yet in use)
-        const int64_t cap_ints = (int64_t)(L.x64 - L.La64) / 4;
-        int64_t chunk = 1024;
-        auto need = [&](int64_t c) {
-            int64_t tab = (int64_t)nlev * ((n + c - 1) / c);
-            return tab + 64 + tab / kScanTile + 64;
-        };
-        while (need(chunk) > cap_ints && chunk < n) chunk *= 2;
-        if (need(chunk) > cap_ints) { set_error("level table does not fit"); return fail(SPUMA_ERR_WORKSPACE_TOO_SMALL); }
-        int nchunks = (int)((n + chunk - 1) / chunk);
-        size_t tab_n = (size_t)nlev * nchunks;
+        // Stable partitions: the count table and its scan temporaries use the
+        // matrix region (48F + 24N bytes, not yet in use).
         int* table = h->at<int>(L.La64);
-        int* tscan = table + tab_n + 64;
-        CU(cudaMemsetAsync(table, 0, 4 * (tab_n + 1), s));
-        int gw = grid_for((int64_t)nchunks * 32, T, h->num_sms);
-        k_level_count<<<gw, T, 0, s>>>(n, (int)chunk, nchunks, level, table);
-        count_launch();
-        CHK(scan_exclusive(table, (int64_t)tab_n, table, tscan, s));
+        const int64_t cap_ints = (int64_t)(L.x64 - L.La64) / 4;
+        auto partition = [&](const int* order, const int* bucket, int nb, int* out_order, int* out_pos,
+                             int* lvl_out) -> spuma_status {
+            int64_t chunk = 1024;
+            auto need = [&](int64_t c) {
+                int64_t tab = (int64_t)nb * ((n + c - 1) / c);
+                return tab + 64 + tab / kScanTile + 64;
+            };
+            while (need(chunk) > cap_ints && chunk < n) chunk *= 2;
+            if (need(chunk) > cap_ints) { set_error("partition table does not fit"); return SPUMA_ERR_WORKSPACE_TOO_SMALL; }
+            int nchunks = (int)((n + chunk - 1) / chunk);
+            size_t tab_n = (size_t)nb * nchunks;
+            int* tscan = table + tab_n + 64;
+            SPUMA_CUDA(cudaMemsetAsync(table, 0, 4 * (tab_n + 1), s));
+            int gw = grid_for((int64_t)nchunks * 32, T, h->num_sms);
+            k_bucket_count<<<gw, T, 0, s>>>(n, (int)chunk, nchunks, order, bucket, table);
+            count_launch();
+            spuma_status ss = scan_exclusive(table, (int64_t)tab_n, table, tscan, s);
+            if (ss != SPUMA_OK) return ss;
+            if (lvl_out) {
+                k_level_starts<<<grid_for(nb + 1, T, h->num_sms), T, 0, s>>>(nb, nchunks, table, n, lvl_out);
+                count_launch();
+            }
+            k_bucket_scatter<<<gw, T, 0, s>>>(n, (int)chunk, nchunks, order, bucket, table, out_order, out_pos);
+            count_launch();
+            SPUMA_CUDA(cudaGetLastError());
+            return SPUMA_OK;
+        };
+        // optional locality order: cells sorted by the Morton code of their
+        // centre (LSD radix sort, four stable passes of 8 bits)
+        const int* key_order = nullptr;
+        if (cell_c) {
+            unsigned* key = h->at<unsigned>(L.b64);
+            int* digit = h->at<int>(L.x32);
+            int* ord_a = h->at<int>(L.r32);
+            int* ord_b = h->at<int>(L.w32);
+            double* bbox = h->at<double>(L.q32);       // 6 doubles per partial block
+            const int nparts = std::min(grid_for(n, T, h->num_sms), (int)((4 * (size_t)n) / 48));
+            const int np = std::max(1, nparts);
+            k_bbox_partial<<<np, T, 0, s>>>(n, cell_c, bbox);
+            k_morton<<<grid_for(n, T, h->num_sms), T, 0, s>>>(n, np, cell_c, bbox, key);
+            count_launch(2);
+            const int* in = nullptr;
+            int* outs[2] = {ord_a, ord_b};
+            for (int pass = 0; pass < 4; pass++) {
+                k_digit<<<grid_for(n, T, h->num_sms), T, 0, s>>>(n, key, 8 * pass, digit);
+                count_launch();
+                CHK(partition(in, digit, 256, outs[pass & 1], nullptr, nullptr));
+                in = outs[pass & 1];
+            }
+            key_order = in;
+        }
         int* lvl = h->at<int>(L.lvl);
-        k_level_starts<<<grid_for(nlev + 1, T, h->num_sms), T, 0, s>>>(nlev, nchunks, table, n, lvl);
-        k_level_scatter<<<gw, T, 0, s>>>(n, (int)chunk, nchunks, level, table, h->at<int>(L.perm),
-                                         h->at<int>(L.iperm));
-        count_launch(2);
+        CHK(partition(key_order, level, nlev, h->at<int>(L.perm), h->at<int>(L.iperm), lvl));
 
         // internal CSR (level order): lower part = neighbour-side faces,
         // upper part = owner-side faces, each in ascending face order

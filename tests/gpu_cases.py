@@ -22,10 +22,10 @@ def dev(a, dtype=None):
     return t.cuda()
 
 
-def mesh_of(c):
+def mesh_of(c, centres=False):
     from paper_2512_22215_gb300 import LduMesh
     m = c.mesh
-    return LduMesh(m.lower, m.upper_addr, m.n_cells)
+    return LduMesh(m.lower, m.upper_addr, m.n_cells, centres=m.c if centres else None)
 
 
 def assemble_gpu(M, c):

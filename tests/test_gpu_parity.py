@@ -13,19 +13,21 @@ from gpu_cases import assemble_gpu, assemble_oracle, bits, case, dev, levels_bru
 pytestmark = pytest.mark.gpu
 
 CASES = [
-    dict(n=16, seed=1),                                               # uniform, natural order
-    dict(n=12, jitter=0.2, permute=True, seed=2, lognormal=True),     # jittered, permuted
-    dict(n=(23, 7, 5), jitter=0.2, permute=True, seed=3, lognormal=True),   # ragged
-    dict(n=(9, 1, 1), seed=4, lognormal=True),                        # 1-D chain
-    dict(n=(2, 2, 1), seed=5),
+    (dict(n=16, seed=1), False),                                              # uniform, natural order
+    (dict(n=12, jitter=0.2, permute=True, seed=2, lognormal=True), False),    # jittered, permuted
+    (dict(n=12, jitter=0.2, permute=True, seed=2, lognormal=True), True),     # same, Morton-ordered levels
+    (dict(n=(23, 7, 5), jitter=0.2, permute=True, seed=3, lognormal=True), True),   # ragged
+    (dict(n=(9, 1, 1), seed=4, lognormal=True), False),                       # 1-D chain
+    (dict(n=(2, 2, 1), seed=5), True),
 ]
-IDS = ["16c-natural", "12c-permuted", "23x7x5-ragged", "chain9", "2x2x1"]
+IDS = ["16c-natural", "12c-permuted", "12c-permuted-morton", "23x7x5-ragged-morton", "chain9", "2x2x1-morton"]
 
 
 @pytest.fixture(scope="module", params=range(len(CASES)), ids=IDS)
 def cm(request):
-    c = case(**CASES[request.param])
-    return c, mesh_of(c)
+    kw, centres = CASES[request.param]
+    c = case(**kw)
+    return c, mesh_of(c, centres)
 
 
 def test_levels_match_bruteforce(cm):

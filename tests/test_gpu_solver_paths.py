@@ -167,7 +167,7 @@ def test_full_size_workloads(n, seed):
     from paper_2512_22215_gb300 import MIXED, SolverControls
     c = case(n, jitter=0.2, permute=True, seed=seed, lognormal=True)
     m = c.mesh
-    M = mesh_of(c)
+    M = mesh_of(c, centres=True)
     up, dg = assemble_gpu(M, c)
     uo, do = assemble_oracle(c)
     assert np.array_equal(bits(up.cpu().numpy()), bits(uo)) and np.array_equal(bits(dg.cpu().numpy()), bits(do))
