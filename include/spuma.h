@@ -54,16 +54,23 @@ typedef enum {
     SPUMA_ERR_DEVICE_TIMEOUT = 8         /* a grid barrier waited past its time limit   */
 } spuma_status;
 
-typedef enum { SPUMA_F64 = 0, SPUMA_MIXED = 1, SPUMA_F32 = 2 } spuma_precision;
+typedef enum { SPUMA_F64 = 0, SPUMA_MIXED = 1, SPUMA_F32 = 2, SPUMA_MIXED_RESTART = 3 } spuma_precision;
 typedef enum { SPUMA_PRECOND_NONE = 0, SPUMA_PRECOND_DIAGONAL = 1, SPUMA_PRECOND_DIC = 2 } spuma_precond;
 
 /* Solver controls, after OpenFOAM's fvSolution entries (paper appendix,
  * fvSolution listing: solver PCG, preconditioner, tolerance, relTol, maxIter,
  * minIter).  Residuals are OpenFOAM's normalised L1 residual
  * sum|b - A x| / normFactor.
- *  precision SPUMA_MIXED: FP32 inner PCG inside FP64 iterative refinement;
- *    inner_rel_tol is the inner solve's relative tolerance, max_outer the
- *    maximum number of refinement steps; max_iter bounds each inner solve.
+ *  precision SPUMA_MIXED: FP32 PCG inside FP64 refinement by reliable
+ *    updates: whenever the FP32 residual has dropped by the factor
+ *    inner_rel_tol since the last update (or claims convergence, or max_iter
+ *    is reached) the FP32 correction is added to the FP64 solution and the
+ *    FP64 residual b - A x replaces the FP32 one; the search direction is
+ *    kept (no Krylov restart).  max_iter bounds the FP32 iterations.
+ *  precision SPUMA_MIXED_RESTART: FP64 iterative refinement around restarted
+ *    FP32 inner solves: inner_rel_tol is the inner solve's relative
+ *    tolerance, max_outer the maximum number of refinement steps, max_iter
+ *    bounds each inner solve.
  *  block_threads: 0 = library default (or the tuned value for batches).   */
 typedef struct {
     int32_t precond;        /* spuma_precond                              */
@@ -201,11 +208,14 @@ spuma_status spuma_precondition(spuma_ldu_t h, int32_t precond, const double* r,
  *   while (n_iter < max_iter and not converged) or n_iter < min_iter,
  *   converged: res < tolerance or (rel_tol > 0 and res < rel_tol res0).
  * x is the initial guess on entry and the solution on exit (original order).
- * precision SPUMA_MIXED: FP32 coefficients, Amul and DIC sweeps inside FP64
- * iterative refinement (FP64 residual, FP64 reductions, FP64 rD):
- *   r = b - A x (FP64); stop when sum|r|/normFactor < tolerance or after
- *   max_outer steps; s = max|r|; inner FP32 PCG on A d = r/s from d = 0 to
- *   inner_rel_tol; x += s d.
+ * precision SPUMA_MIXED / SPUMA_MIXED_RESTART: FP32 coefficients, Amul and
+ * DIC sweeps inside FP64 refinement (FP64 residual, FP64 reductions, FP64
+ * rD).  Reliable updates (MIXED): FP32 PCG on r; when sum|r32| fell below
+ * inner_rel_tol times its value at the last update: x += xs, r = b - A x in
+ * FP64, r32 = float(r), p kept; stop when the FP64 residual converges.
+ * Restarted (MIXED_RESTART): r = b - A x (FP64); stop when sum|r|/normFactor
+ * < tolerance or after max_outer steps; s = max|r|; inner FP32 PCG on
+ * A d = r/s from d = 0 to inner_rel_tol; x += s d.
  * The whole solve is one persistent cooperative kernel (plus the prepare
  * kernels): no host round trip per iteration.  perf is a DEVICE pointer.
  * ---------------------------------------------------------------------- */

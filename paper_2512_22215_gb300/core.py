@@ -17,7 +17,7 @@ class SolverControls:
     precision: int = F64
     tolerance: float = 1e-8
     rel_tol: float = 0.0
-    inner_rel_tol: float = 1e-4
+    inner_rel_tol: float = 1e-2
     max_iter: int = 20000
     min_iter: int = 0
     max_outer: int = 30

@@ -37,15 +37,40 @@ __device__ __forceinline__ Mat<float> mat_of<float>(const SolveArgs& a)
     return Mat<float>{a.Lptr, a.Lcol, a.La32, a.Lc32, a.Uptr, a.Ucol, a.Ua32, a.Uc32, a.d32, a.rD32};
 }
 
+// One row's multiply-add chain over entries [e0, e1) (DESC: from e1-1 down
+// to e0), taking the entries in groups of four: the column and coefficient
+// loads of a group are issued together, then its gathers, then the FMAs in
+// entry order -- two memory round trips per group instead of two per entry.
+template <class T, bool DESC, bool NEG>
+__device__ __forceinline__ T row_chain(T acc, int e0, int e1, const int* col, const T* coef, const T* vec)
+{
+    constexpr int G = 4;
+    for (int e = DESC ? e1 - 1 : e0; DESC ? e >= e0 : e < e1; e += DESC ? -G : G) {
+        int c[G];
+        T k[G], v[G];
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            const int ej = DESC ? e - j : e + j;
+            const bool ok = DESC ? ej >= e0 : ej < e1;
+            c[j] = ok ? __ldg(col + ej) : -1;
+            k[j] = ok ? coef[ej] : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < G; j++) v[j] = c[j] >= 0 ? vec[c[j]] : T(0);
+#pragma unroll
+        for (int j = 0; j < G; j++)
+            if (c[j] >= 0) acc = fmadd(NEG ? -k[j] : k[j], v[j], acc);
+    }
+    return acc;
+}
+
 // y_p = d_p x_p + lower entries (ascending face) + upper entries (ascending face)
 template <class T>
-__device__ __forceinline__ T amul_row(const Mat<T>& A, const T* __restrict__ x, int p)
+__device__ __forceinline__ T amul_row(const Mat<T>& A, const T* x, int p)
 {
     T y = mul_rn(A.d[p], x[p]);
-    const int l0 = A.Lptr[p], l1 = A.Lptr[p + 1];
-    for (int e = l0; e < l1; e++) y = fmadd(A.La[e], x[A.Lcol[e]], y);
-    const int u0 = A.Uptr[p], u1 = A.Uptr[p + 1];
-    for (int e = u0; e < u1; e++) y = fmadd(A.Ua[e], x[A.Ucol[e]], y);
+    y = row_chain<T, false, false>(y, __ldg(A.Lptr + p), __ldg(A.Lptr + p + 1), A.Lcol, A.La, x);
+    y = row_chain<T, false, false>(y, __ldg(A.Uptr + p), __ldg(A.Uptr + p + 1), A.Ucol, A.Ua, x);
     return y;
 }
 
@@ -379,8 +404,7 @@ __device__ bool dic_forward_thread(const SolveArgs& a, const Mat<T>& A, Vecs<T> 
                 acc.add(fabs(rr));
             }
             T ww = mul_rn(A.rD[p], rr);
-            const int e1 = A.Lptr[p + 1];
-            for (int e = A.Lptr[p]; e < e1; e++) ww = fmadd(-A.Lc[e], v.w[A.Lcol[e]], ww);
+            ww = row_chain<T, false, true>(ww, __ldg(A.Lptr + p), __ldg(A.Lptr + p + 1), A.Lcol, A.Lc, v.w);
             v.w[p] = ww;
         }
         if (L == a.nlev - 1 && pending) {
@@ -403,8 +427,7 @@ __device__ bool dic_backward_thread(const SolveArgs& a, const Mat<T>& A, Vecs<T>
         const int r0 = a.lvl[L], r1 = a.lvl[L + 1];
         for (int p = r0 + it.first; p < r1; p += it.stride) {
             T ww = v.w[p];
-            const int e0 = A.Uptr[p];
-            for (int e = A.Uptr[p + 1] - 1; e >= e0; e--) ww = fmadd(-A.Uc[e], v.w[A.Ucol[e]], ww);
+            ww = row_chain<T, true, true>(ww, __ldg(A.Uptr + p), __ldg(A.Uptr + p + 1), A.Ucol, A.Uc, v.w);
             v.w[p] = ww;
             acc.prod(ww, v.r[p]);
         }
@@ -434,6 +457,109 @@ __device__ __forceinline__ bool dic_backward(const SolveArgs& a, const Mat<T>& A
     return dic_backward_thread<T>(a, A, v, want_rho, g, pc);
 }
 
+// Diagonal / no preconditioning in one pass, fused with the pending x/r
+// update; returns sum|r| (of the updated r) and rho = w.r through t[0], t[1].
+template <class T>
+__device__ bool diag_pass(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool pending, T alpha, const Group& g,
+                          double (&t)[2])
+{
+    RowIter it = rows_of(g);
+    Acc<T> ares, arho;
+    for (int p = it.first; p < a.n; p += it.stride) {
+        T rr = v.r[p];
+        if (pending) {
+            v.x[p] = fmadd(alpha, v.p[p], v.x[p]);
+            rr = fmadd(-alpha, v.q[p], rr);
+            v.r[p] = rr;
+            ares.add(fabs(rr));
+        }
+        T ww = a.precond == SPUMA_PRECOND_DIAGONAL ? mul_rn(A.rD[p], rr) : rr;
+        v.w[p] = ww;
+        arho.prod(ww, rr);
+    }
+    double acc[2] = {ares.value(), arho.value()};
+    block_reduce_store<2>(acc, a.partials, SL_A, g.bid);
+    if (!group_sync(g)) return false;
+    grid_reduce_read<2>(t, a.partials, SL_A, g.nblocks);
+    return true;
+}
+
+// p = w (first) or w + beta p
+template <class T>
+__device__ bool search_direction(const SolveArgs& a, Vecs<T> v, bool first, T beta, const Group& g)
+{
+    RowIter it = rows_of(g);
+    for (int p = it.first; p < a.n; p += it.stride) v.p[p] = first ? v.w[p] : fmadd(beta, v.p[p], v.w[p]);
+    return group_sync(g);
+}
+
+// q = A p and sigma = q.p
+template <class T, int RM>
+__device__ bool amul_sigma(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const Group& g, double* sigma)
+{
+    Acc<T> asig;
+    if (RM) {
+        const WarpIter wi = warps_of(g);
+        for (int p0 = 32 * wi.first; p0 < a.n; p0 += 32 * wi.stride) {
+            const int nv = min(32, a.n - p0), p = p0 + wi.lane;
+            const T qq = warp_amul_row<T>(A, v.p, p0, nv, wi.lane);
+            if (wi.lane < nv) {
+                v.q[p] = qq;
+                asig.prod(qq, v.p[p]);
+            }
+        }
+    } else {
+        RowIter it = rows_of(g);
+        for (int p = it.first; p < a.n; p += it.stride) {
+            const T qq = amul_row<T>(A, v.p, p);
+            v.q[p] = qq;
+            asig.prod(qq, v.p[p]);
+        }
+    }
+    double sacc[1] = {asig.value()};
+    block_reduce_store<1>(sacc, a.partials, SL_C, g.bid);
+    if (!group_sync(g)) return false;
+    double sg[1];
+    grid_reduce_read<1>(sg, a.partials, SL_C, g.nblocks);
+    *sigma = sg[0];
+    return true;
+}
+
+// w = M^-1 r (fused with the pending update); returns the updated sum|r| when
+// pending, and rho = w.r.  For DIC the residual norm is known after the
+// forward sweep; `after_fwd` runs there (it may replace r and ask for the
+// forward sweep to be redone) before the backward sweep computes rho.
+template <class T, int RM, class AfterFwd>
+__device__ int precondition(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool pending, T alpha, const Group& g,
+                            PhaseClock& pc, double* rho, AfterFwd after_fwd)
+{
+    double ressum = 0.0;
+    if (a.precond == SPUMA_PRECOND_DIC) {
+        if (!dic_forward<T, RM>(a, A, v, pending, alpha, g, pc)) return -1;
+        if (pending) {
+            double t[1];
+            grid_reduce_read<1>(t, a.partials, SL_A, g.nblocks);
+            ressum = t[0];
+        }
+        const int act = after_fwd(ressum);       // 0 continue, 1 stop, 2 redo (r replaced), -1 error
+        if (act == 1 || act < 0) return act;
+        if (act == 2 && !dic_forward<T, RM>(a, A, v, false, T(0), g, pc)) return -1;
+        if (!dic_backward<T, RM>(a, A, v, true, g, pc)) return -1;
+        double t[1];
+        grid_reduce_read<1>(t, a.partials, SL_B, g.nblocks);
+        *rho = t[0];
+        return 0;
+    }
+    double t[2];
+    if (!diag_pass<T>(a, A, v, pending, alpha, g, t)) return -1;
+    pc.lap(CK_DIAG);
+    const int act = after_fwd(t[0]);
+    if (act == 1 || act < 0) return act;
+    if (act == 2 && !diag_pass<T>(a, A, v, false, T(0), g, t)) return -1;
+    *rho = t[1];
+    return 0;
+}
+
 // PCG iterations on (A, v.r) from the current v.x (OpenFOAM recurrences).
 // Returns the iteration count, or -1 when a device error stopped the group.
 template <class T, int RM>
@@ -441,7 +567,6 @@ __device__ int pcg_loop(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, double n
                         double rel_tol, int max_iter, int min_iter, double* res_out, int* singular,
                         const Group& g)
 {
-    RowIter it = rows_of(g);
     PhaseClock pc(a.phase_clk, g.bid);
     double res = res0;
     *res_out = res;
@@ -452,87 +577,148 @@ __device__ int pcg_loop(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, double n
     bool pending = false;
     for (;;) {
         rho_old = rho;
-        if (a.precond == SPUMA_PRECOND_DIC) {
-            if (!dic_forward<T, RM>(a, A, v, pending, alpha, g, pc)) return -1;
-            if (pending) {
-                double t[1];
-                grid_reduce_read<1>(t, a.partials, SL_A, g.nblocks);
-                res = t[0] / nfac;
-                n_it++;
-                if (!((n_it < max_iter && !converged(res, res0, tol, rel_tol)) || n_it < min_iter)) break;
-            }
-            if (!dic_backward<T, RM>(a, A, v, true, g, pc)) return -1;
-            double t[1];
-            grid_reduce_read<1>(t, a.partials, SL_B, g.nblocks);
-            rho = t[0];
-        } else {
-            Acc<T> ares, arho;
-            for (int p = it.first; p < a.n; p += it.stride) {
-                T rr = v.r[p];
-                if (pending) {
-                    v.x[p] = fmadd(alpha, v.p[p], v.x[p]);
-                    rr = fmadd(-alpha, v.q[p], rr);
-                    v.r[p] = rr;
-                    ares.add(fabs(rr));
-                }
-                T ww = a.precond == SPUMA_PRECOND_DIAGONAL ? mul_rn(A.rD[p], rr) : rr;
-                v.w[p] = ww;
-                arho.prod(ww, rr);
-            }
-            double acc[2] = {ares.value(), arho.value()};
-            block_reduce_store<2>(acc, a.partials, SL_A, g.bid);
-            if (!group_sync(g)) return -1;
-            pc.lap(CK_DIAG);
-            double t[2];
-            grid_reduce_read<2>(t, a.partials, SL_A, g.nblocks);
-            if (pending) {
-                res = t[0] / nfac;
-                n_it++;
-                if (!((n_it < max_iter && !converged(res, res0, tol, rel_tol)) || n_it < min_iter)) break;
-            }
-            rho = t[1];
-        }
-        // search direction
+        const int act = precondition<T, RM>(a, A, v, pending, alpha, g, pc, &rho, [&](double ressum) {
+            if (!pending) return 0;
+            res = ressum / nfac;
+            n_it++;
+            return ((n_it < max_iter && !converged(res, res0, tol, rel_tol)) || n_it < min_iter) ? 0 : 1;
+        });
+        if (act < 0) return -1;
+        if (act == 1) break;
         const bool first = n_it == 0;
-        const T beta = first ? (T)0 : (T)(rho / rho_old);
-        for (int p = it.first; p < a.n; p += it.stride) v.p[p] = first ? v.w[p] : fmadd(beta, v.p[p], v.w[p]);
-        if (!group_sync(g)) return -1;
+        if (!search_direction<T>(a, v, first, first ? (T)0 : (T)(rho / rho_old), g)) return -1;
         pc.lap(CK_PUPD);
-        // q = A p, sigma = q.p
-        Acc<T> asig;
-        if (RM) {
-            const WarpIter wi = warps_of(g);
-            for (int p0 = 32 * wi.first; p0 < a.n; p0 += 32 * wi.stride) {
-                const int nv = min(32, a.n - p0), p = p0 + wi.lane;
-                const T qq = warp_amul_row<T>(A, v.p, p0, nv, wi.lane);
-                if (wi.lane < nv) {
-                    v.q[p] = qq;
-                    asig.prod(qq, v.p[p]);
-                }
-            }
-        } else {
-            for (int p = it.first; p < a.n; p += it.stride) {
-                const T qq = amul_row<T>(A, v.p, p);
-                v.q[p] = qq;
-                asig.prod(qq, v.p[p]);
-            }
-        }
-        double sacc[1] = {asig.value()};
-        block_reduce_store<1>(sacc, a.partials, SL_C, g.bid);
-        if (!group_sync(g)) return -1;
+        double sigma;
+        if (!amul_sigma<T, RM>(a, A, v, g, &sigma)) return -1;
         pc.lap(CK_AMUL);
         pc.count(CK_ITERS);
-        double sg[1];
-        grid_reduce_read<1>(sg, a.partials, SL_C, g.nblocks);
-        if (fabs(sg[0]) / nfac < 1e-300) {
+        if (fabs(sigma) / nfac < 1e-300) {
             *singular = 1;
             break;
         }
-        alpha = (T)(rho / sg[0]);
+        alpha = (T)(rho / sigma);
         pending = true;
     }
     *res_out = res;
     return n_it;
+}
+
+// FP64 refinement step of the mixed forms: x += xs (FP32 correction, reset to
+// 0), then r = b - A64 x with sum|r| (and max|r|), and r32 = float(r) (or
+// float(r / max|r|) for the restarted form, which scales).
+template <int RM>
+__device__ bool refine_residual(const SolveArgs& a, const Group& g, bool fold, double* ressum, double* rmax)
+{
+    RowIter it = rows_of(g);
+    const Mat<double> A64 = mat_of<double>(a);
+    if (fold) {
+        for (int p = it.first; p < a.n; p += it.stride) {
+            a.x[p] = __dadd_rn(a.x[p], (double)a.xi[p]);
+            a.xi[p] = 0.0f;
+        }
+        if (!group_sync(g)) return false;
+    }
+    double acc[1] = {0.0}, mx[1] = {0.0};
+    if (!RM) {
+        for (int p = it.first; p < a.n; p += it.stride) {
+            const double rr = a.b[p] - amul_row<double>(A64, a.x, p);
+            a.r[p] = rr;
+            a.ri[p] = (float)rr;
+            acc[0] += fabs(rr);
+            mx[0] = fmax(mx[0], fabs(rr));
+        }
+    } else {
+        const WarpIter wi = warps_of(g);
+        for (int p0 = 32 * wi.first; p0 < a.n; p0 += 32 * wi.stride) {
+            const int nv = min(32, a.n - p0), p = p0 + wi.lane;
+            const double ax = warp_amul_row<double>(A64, a.x, p0, nv, wi.lane);
+            if (wi.lane < nv) {
+                const double rr = a.b[p] - ax;
+                a.r[p] = rr;
+                a.ri[p] = (float)rr;
+                acc[0] += fabs(rr);
+                mx[0] = fmax(mx[0], fabs(rr));
+            }
+        }
+    }
+    block_reduce_store<1>(acc, a.partials, SL_D, g.bid);
+    block_max_store<1>(mx, a.partials, SL_D + 1, g.bid);
+    if (!group_sync(g)) return false;
+    double t[1], m[1];
+    grid_reduce_read<1>(t, a.partials, SL_D, g.nblocks);
+    grid_reduce_read<1, true>(m, a.partials, SL_D + 1, g.nblocks);
+    *ressum = t[0];
+    *rmax = m[0];
+    return true;
+}
+
+// Mixed precision with reliable updates: FP32 PCG whose correction and
+// residual are replaced by FP64 ones (x += xs; r = b - A64 x) whenever the
+// FP32 residual has dropped by inner_rel_tol since the last replacement, the
+// FP32 residual claims convergence, or max_iter is reached; the search
+// direction is kept, so the Krylov space is never restarted.
+template <int RM>
+__device__ bool solve_mixed_reliable(const SolveArgs& a, const Group& g, double nfac, double res0,
+                                     spuma_solver_perf& pf)
+{
+    RowIter it = rows_of(g);
+    const Mat<float> A32 = mat_of<float>(a);
+    Vecs<float> v{a.xi, a.ri, a.wi, a.pi, a.qi};
+    PhaseClock pc(a.phase_clk, g.bid);
+    const double delta = a.inner_rel_tol;
+    double res = res0, rupd = res0, rho = 1.0, rho_old;
+    int n_it = 0, updates = 0, singular = 0;
+    float alpha = 0.0f;
+    bool pending = false, ok = true;
+    if (!converged(res0, res0, a.tol, a.rel_tol)) {
+        for (int p = it.first; p < a.n; p += it.stride) {
+            v.r[p] = (float)a.r[p];
+            v.x[p] = 0.0f;
+        }
+        if (!group_sync(g)) return false;
+        for (;;) {
+            rho_old = rho;
+            const int act = precondition<float, RM>(a, A32, v, pending, alpha, g, pc, &rho, [&](double ressum) {
+                if (!pending) return 0;
+                n_it++;
+                const double ress = ressum / nfac;
+                if (!(ress < delta * rupd || converged(ress, res0, a.tol, a.rel_tol) || n_it >= a.max_iter)) return 0;
+                double rs, rm;
+                if (!refine_residual<RM>(a, g, true, &rs, &rm)) return -1;
+                pc.lap(CK_RESID);
+                updates++;
+                res = rs / nfac;
+                if (converged(res, res0, a.tol, a.rel_tol) || n_it >= a.max_iter) return 1;
+                rupd = res;
+                return 2;
+            });
+            if (act < 0) return false;
+            if (act == 1) break;
+            const bool first = n_it == 0;
+            if (!search_direction<float>(a, v, first, first ? 0.0f : (float)(rho / rho_old), g)) return false;
+            pc.lap(CK_PUPD);
+            double sigma;
+            if (!amul_sigma<float, RM>(a, A32, v, g, &sigma)) return false;
+            pc.lap(CK_AMUL);
+            pc.count(CK_ITERS);
+            if (fabs(sigma) / nfac < 1e-300) {
+                singular = 1;
+                double rs, rm;
+                ok = refine_residual<RM>(a, g, true, &rs, &rm);
+                res = rs / nfac;
+                break;
+            }
+            alpha = (float)(rho / sigma);
+            pending = true;
+        }
+    }
+    pf.initial_residual = res0;
+    pf.final_residual = res;
+    pf.n_iter = n_it;
+    pf.n_outer = updates;
+    pf.converged = converged(res, res0, a.tol, a.rel_tol);
+    pf.singular = singular;
+    return ok;
 }
 
 // x = x_orig (or 0), b = b_orig in internal order; q = A x; r = b - q;
@@ -587,48 +773,23 @@ __device__ void phase_store_x(const SolveArgs& a, const Group& g)
     for (int p = it.first; p < a.n; p += it.stride) a.x_orig[a.perm[p]] = a.x[p];
 }
 
-// Mixed precision: FP64 refinement around FP32 inner PCG.
+// Mixed precision, restarted form: FP64 refinement around FP32 inner PCG
+// solves of A d = r / max|r| from d = 0 to inner_rel_tol.
 template <int RM>
-__device__ bool solve_mixed(const SolveArgs& a, const Group& g, double nfac, spuma_solver_perf& pf)
+__device__ bool solve_mixed_restart(const SolveArgs& a, const Group& g, double nfac, spuma_solver_perf& pf)
 {
     RowIter it = rows_of(g);
-    const Mat<double> A64 = mat_of<double>(a);
     const Mat<float> A32 = mat_of<float>(a);
     Vecs<float> vi{a.xi, a.ri, a.wi, a.pi, a.qi};
     int outer = 0, total = 0, singular = 0;
     double res = 0.0, res0 = 0.0;
     for (;;) {
-        double acc[1] = {0.0}, mx[1] = {0.0};
-        if (!RM) {
-            for (int p = it.first; p < a.n; p += it.stride) {
-                const double rr = a.b[p] - amul_row<double>(A64, a.x, p);
-                a.r[p] = rr;
-                acc[0] += fabs(rr);
-                mx[0] = fmax(mx[0], fabs(rr));
-            }
-        } else {
-            const WarpIter wi = warps_of(g);
-            for (int p0 = 32 * wi.first; p0 < a.n; p0 += 32 * wi.stride) {
-                const int nv = min(32, a.n - p0), p = p0 + wi.lane;
-                const double ax = warp_amul_row<double>(A64, a.x, p0, nv, wi.lane);
-                if (wi.lane < nv) {
-                    const double rr = a.b[p] - ax;
-                    a.r[p] = rr;
-                    acc[0] += fabs(rr);
-                    mx[0] = fmax(mx[0], fabs(rr));
-                }
-            }
-        }
-        block_reduce_store<1>(acc, a.partials, SL_A, g.bid);
-        block_max_store<1>(mx, a.partials, SL_B, g.bid);
-        if (!group_sync(g)) return false;
-        double t[1], m[1];
-        grid_reduce_read<1>(t, a.partials, SL_A, g.nblocks);
-        grid_reduce_read<1, true>(m, a.partials, SL_B, g.nblocks);
-        res = t[0] / nfac;
+        double rs, rm;
+        if (!refine_residual<RM>(a, g, false, &rs, &rm)) return false;
+        res = rs / nfac;
         if (outer == 0) res0 = res;
         if (res < a.tol || outer >= a.max_outer || singular) break;
-        const double s = m[0];
+        const double s = rm;
         if (s == 0.0) break;
         Acc<float> ain;
         for (int p = it.first; p < a.n; p += it.stride) {
@@ -704,7 +865,9 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
         ok = phase_init(a, g, &nfac, &res0);
         if (ok) {
             if (a.precision == SPUMA_MIXED) {
-                ok = solve_mixed<RM>(a, g, nfac, pf);
+                ok = solve_mixed_reliable<RM>(a, g, nfac, res0, pf);
+            } else if (a.precision == SPUMA_MIXED_RESTART) {
+                ok = solve_mixed_restart<RM>(a, g, nfac, pf);
             } else {
                 Vecs<double> v{a.x, a.r, a.w, a.p, a.q};
                 double res;
@@ -926,9 +1089,11 @@ bool ctl_ok(const spuma_solver_controls* c)
 {
     if (!c) return false;
     if (c->precond < 0 || c->precond > 2) return false;
-    if (c->precision != SPUMA_F64 && c->precision != SPUMA_MIXED) return false;
+    if (c->precision != SPUMA_F64 && c->precision != SPUMA_MIXED && c->precision != SPUMA_MIXED_RESTART) return false;
     if (!(c->tolerance >= 0.0) || !(c->rel_tol >= 0.0) || c->max_iter < 0 || c->min_iter < 0) return false;
-    if (c->precision == SPUMA_MIXED && (!(c->inner_rel_tol > 0.0) || c->max_outer < 0)) return false;
+    if ((c->precision == SPUMA_MIXED || c->precision == SPUMA_MIXED_RESTART) &&
+        (!(c->inner_rel_tol > 0.0) || c->max_outer < 0))
+        return false;
     return true;
 }
 

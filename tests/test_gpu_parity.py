@@ -127,20 +127,30 @@ def test_pcg_controls_and_x0(cm):
 
 
 @pytest.mark.parametrize("precond", [1, 2])
-def test_mixed_refinement(cm, precond):
-    from paper_2512_22215_gb300 import MIXED, SolverControls
+@pytest.mark.parametrize("form", ["reliable", "restart"])
+def test_mixed_refinement(cm, precond, form):
+    from paper_2512_22215_gb300 import MIXED, MIXED_RESTART, SolverControls
     c, M = cm
     m = c.mesh
     uo, do = assemble_oracle(c)
-    ctl = SolverControls(precond=precond, precision=MIXED, tolerance=1e-10, inner_rel_tol=1e-4, max_outer=30)
+    if form == "reliable":
+        ctl = SolverControls(precond=precond, precision=MIXED, tolerance=1e-10, inner_rel_tol=1e-2)
+        xo, po = oracle.mixed_reliable(m.lower, m.upper_addr, do, uo, c.b, precond=precond, tol=1e-10, delta=1e-2)
+    else:
+        ctl = SolverControls(precond=precond, precision=MIXED_RESTART, tolerance=1e-10, inner_rel_tol=1e-4,
+                             max_outer=30)
+        xo, po = oracle.mixed_ir(m.lower, m.upper_addr, do, uo, c.b, precond=precond, tol=1e-10, inner_rel_tol=1e-4)
     x, p = M.solve(dev(do), dev(uo), dev(c.b), None, ctl)
     x = x.cpu().numpy()
     assert p["converged"] == 1 and p["status"] == 0 and p["n_outer"] >= 1
+    # FP32 trajectories follow the rounding of float(alpha), float(beta): the
+    # iteration counts agree within 15 %; the FP64 residual and the solution
+    # error below are the parity criteria
+    assert abs(p["n_iter"] - po["n_iter"]) <= max(3, (3 * po["n_iter"]) // 20)
     # FP64 true residual of the refined solution (oracle Amul)
     r = c.b - oracle.amul(m.lower, m.upper_addr, do, uo, x)
     assert np.abs(r).sum() / (np.abs(c.b).sum() + 1e-20) < 1e-10
     xs, _ = oracle.pcg(m.lower, m.upper_addr, do, uo, c.b, precond=2, tol=1e-15, max_iter=20000)
-    xo, po = oracle.mixed_ir(m.lower, m.upper_addr, do, uo, c.b, precond=precond, tol=1e-10, inner_rel_tol=1e-4)
     # both refined solutions sit within the same residual-implied distance of x*
     e_gpu = np.linalg.norm(x - xs) / np.linalg.norm(xs)
     e_ora = np.linalg.norm(xo - xs) / np.linalg.norm(xs)
