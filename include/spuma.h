@@ -224,6 +224,30 @@ spuma_status spuma_pcg_solve(spuma_ldu_t h, const double* diag, const double* up
                              spuma_solver_perf* perf, spuma_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * The same PCG solve without any device allocation (the paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc, such as a
+ * solver plugin inside an application that owns the device allocator, or a
+ * code path that must not pay cudaMalloc's implicit synchronisation).  The
+ * mesh topology and all solver scratch live in one static device array of
+ * spuma_static_workspace_bytes() bytes (32 MiB, enough for hex meshes of
+ * about 90 thousand cells) that every GPU loading the library holds until the
+ * process exits; a larger mesh is rejected with SPUMA_ERR_WORKSPACE_TOO_SMALL
+ * before any device work.  The caller passes the addressing, the
+ * coefficients, b, x (initial guess in, solution out) and perf, all device
+ * pointers, as for spuma_ldu_create + spuma_pcg_solve, which this call
+ * performs in one go (the topology build waits for the stream).  The first
+ * call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  Every call
+ * reuses the same array and each call clears what it needs, but calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on it.
+ * ---------------------------------------------------------------------- */
+size_t spuma_static_workspace_bytes(void);
+spuma_status spuma_pcg_solve_static(int32_t n_cells, int32_t n_faces, const int32_t* lower_addr,
+                                    const int32_t* upper_addr, const double* diag, const double* upper,
+                                    const double* b, double* x, const spuma_solver_controls* ctl,
+                                    spuma_solver_perf* perf, spuma_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Adjoint of x = A^-1 b for a loss L(x), given x and dldx = dL/dx:
  *   A lambda = dldx (A symmetric: A^T = A, same PCG, lambda from 0);
  *   dL/db = lambda;  dL/dupper_f = -(lambda_{l(f)} x_{u(f)} + lambda_{u(f)} x_{l(f)});

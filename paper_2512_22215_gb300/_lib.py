@@ -62,6 +62,8 @@ _SIGS = {
     "spuma_permute": (_I, [_H, _I, _P, _P, _P]),
     "spuma_precondition": (_I, [_H, _I, _P, _P, _P]),
     "spuma_pcg_solve": (_I, [_H, _P, _P, _P, _P, C.POINTER(Controls), _P, _P]),
+    "spuma_static_workspace_bytes": (C.c_size_t, []),
+    "spuma_pcg_solve_static": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, C.POINTER(Controls), _P, _P]),
     "spuma_pcg_adjoint": (_I, [_H, _P, _P, _P, _P, _P, _P, _P, C.POINTER(Controls), _P, _P]),
     "spuma_batch_create": (_I, [_I, C.POINTER(_H), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                 C.POINTER(Controls), _P, _I, _P, C.POINTER(_H)]),
