@@ -28,12 +28,17 @@ uint64_t barrier_timeout_ns();
         if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
     } while (0)
 
-// Device status words (int32): [0] status, [1] first offending cell/face.
-enum DevStatus { DS_STATUS = 0, DS_INDEX = 1, DS_LEVELS_CHANGED = 2, DS_MAXLEVEL = 3 };
+// Device status words (int32): [0] status, [1] first offending cell/face,
+// [32] the grid barrier's arrival word (its own 128-byte line), whose top bit
+// tells every waiting block that an error was recorded.
+enum DevStatus { DS_STATUS = 0, DS_INDEX = 1, DS_LEVELS_CHANGED = 2, DS_MAXLEVEL = 3, DS_BARRIER = 32 };
+constexpr unsigned kErrBit = 0x80000000u;
 
 __device__ __forceinline__ void flag_error(int* st, int code, int index)
 {
     if (atomicCAS(st + DS_STATUS, 0, code) == 0) st[DS_INDEX] = index;
+    __threadfence();
+    atomicOr(reinterpret_cast<unsigned*>(st + DS_BARRIER), kErrBit);
 }
 
 // ------------------------------------------------------- memory helpers --
@@ -72,12 +77,14 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 
 // --------------------------------------------------------- grid barrier --
 // A group of co-resident blocks (a cooperative launch guarantees residency)
-// synchronises on an arrival counter and a generation word that sit on
-// separate 128-byte lines.  Every wait is bounded by a time limit: when it
-// expires the block records SPUMA_ERR_DEVICE_TIMEOUT and the caller unwinds.
+// synchronises on one arrival word that only grows during a launch: a block
+// arriving as the k-th (0-based) waits until the word reaches the next
+// multiple of the group size.  No generation read before arriving, no status
+// reload after: an error sets the word's top bit, which ends every wait.
+// Every wait is bounded by a time limit: when it expires the block records
+// SPUMA_ERR_DEVICE_TIMEOUT and the caller unwinds.
 struct Group {
-    unsigned* count;       // arrival counter
-    unsigned* gen;         // generation
+    unsigned* word;        // arrival word (status + DS_BARRIER)
     int* status;           // device status words
     int nblocks;           // blocks in the group
     int bid;               // this block's index in the group
@@ -87,30 +94,37 @@ struct Group {
 // Returns true when the caller may continue (no error recorded anywhere).
 __device__ __forceinline__ bool group_sync(const Group& g)
 {
+    __shared__ int s_err;
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned gen0 = ld_acquire(g.gen);
         __threadfence();
-        unsigned arrived = atom_add_acq_rel(g.count, 1u);
-        if (arrived == (unsigned)g.nblocks - 1u) {
-            *(volatile unsigned*)g.count = 0u;
-            __threadfence();
-            st_release(g.gen, gen0 + 1u);
-        } else {
-            unsigned long long t0 = global_timer_ns();
-            while (ld_acquire(g.gen) == gen0) {
-                if (ld_volatile_int(g.status) != 0) break;
-                if (global_timer_ns() - t0 > g.timeout_ns) {
-                    flag_error(g.status, SPUMA_ERR_DEVICE_TIMEOUT, g.bid);
-                    break;
+        const unsigned old = atom_add_acq_rel(g.word, 1u);
+        bool err = (old & kErrBit) != 0;
+        if (!err) {
+            const unsigned cnt = old & ~kErrBit;
+            const unsigned target = (cnt / (unsigned)g.nblocks + 1u) * (unsigned)g.nblocks;
+            if (cnt + 1u != target) {
+                const unsigned long long t0 = global_timer_ns();
+                for (;;) {
+                    const unsigned w = ld_acquire(g.word);
+                    if (w & kErrBit) {
+                        err = true;
+                        break;
+                    }
+                    if ((w & ~kErrBit) >= target) break;
+                    if (global_timer_ns() - t0 > g.timeout_ns) {
+                        flag_error(g.status, SPUMA_ERR_DEVICE_TIMEOUT, g.bid);
+                        err = true;
+                        break;
+                    }
                 }
-                __nanosleep(32);
             }
         }
         __threadfence();
+        s_err = err ? 1 : 0;
     }
     __syncthreads();
-    return ld_volatile_int(g.status) == 0;
+    return s_err == 0;
 }
 
 // ------------------------------------------------------------ reductions --

@@ -386,33 +386,69 @@ __device__ bool dic_backward_warp(const SolveArgs& a, const Mat<T>& A, Vecs<T> v
     return true;
 }
 
-// One thread per row variants of the two sweeps.
+// One thread per row variants of the two sweeps.  The small last levels
+// (level >= tail_from, each at most one row per thread of a block) are run by
+// the group's first block alone with block-level barriers, followed by one
+// grid barrier, instead of one grid barrier per level.
+template <class T>
+__device__ __forceinline__ void fwd_rows(const Mat<T>& A, Vecs<T> v, bool pending, T alpha, int r0, int r1, int first,
+                                         int stride, Acc<T>& acc)
+{
+    for (int p = r0 + first; p < r1; p += stride) {
+        T rr = v.r[p];
+        if (pending) {
+            v.x[p] = fmadd(alpha, v.p[p], v.x[p]);
+            rr = fmadd(-alpha, v.q[p], rr);
+            v.r[p] = rr;
+            acc.add(fabs(rr));
+        }
+        T ww = mul_rn(A.rD[p], rr);
+        ww = row_chain<T, false, true>(ww, __ldg(A.Lptr + p), __ldg(A.Lptr + p + 1), A.Lcol, A.Lc, v.w);
+        v.w[p] = ww;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ void bwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int r1, int first, int stride,
+                                         Acc<T>& acc)
+{
+    for (int p = r0 + first; p < r1; p += stride) {
+        T ww = v.w[p];
+        ww = row_chain<T, true, true>(ww, __ldg(A.Uptr + p), __ldg(A.Uptr + p + 1), A.Ucol, A.Uc, v.w);
+        v.w[p] = ww;
+        acc.prod(ww, v.r[p]);
+    }
+}
+
 template <class T>
 __device__ bool dic_forward_thread(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool pending, T alpha,
                                    const Group& g, PhaseClock& pc)
 {
     RowIter it = rows_of(g);
     Acc<T> acc;
-    for (int L = 0; L < a.nlev; L++) {
-        const int r0 = a.lvl[L], r1 = a.lvl[L + 1];
-        for (int p = r0 + it.first; p < r1; p += it.stride) {
-            T rr = v.r[p];
-            if (pending) {
-                v.x[p] = fmadd(alpha, v.p[p], v.x[p]);
-                rr = fmadd(-alpha, v.q[p], rr);
-                v.r[p] = rr;
-                acc.add(fabs(rr));
-            }
-            T ww = mul_rn(A.rD[p], rr);
-            ww = row_chain<T, false, true>(ww, __ldg(A.Lptr + p), __ldg(A.Lptr + p + 1), A.Lcol, A.Lc, v.w);
-            v.w[p] = ww;
-        }
+    const int tail = min(a.tail_from, a.nlev);
+    for (int L = 0; L < tail; L++) {
+        fwd_rows<T>(A, v, pending, alpha, a.lvl[L], a.lvl[L + 1], it.first, it.stride, acc);
         if (L == a.nlev - 1 && pending) {
             double t[1] = {acc.value()};
             block_reduce_store<1>(t, a.partials, SL_A, g.bid);
         }
         if (!group_sync(g)) return false;
         pc.lap(CK_FWD + min(L, 63));
+    }
+    if (tail < a.nlev) {
+        if (g.bid == 0) {
+            for (int L = tail; L < a.nlev; L++) {
+                fwd_rows<T>(A, v, pending, alpha, a.lvl[L], a.lvl[L + 1], (int)threadIdx.x, (int)blockDim.x, acc);
+                __syncthreads();
+            }
+        }
+        if (pending) {
+            double t[1] = {acc.value()};
+            block_reduce_store<1>(t, a.partials, SL_A, g.bid);
+        }
+        if (!group_sync(g)) return false;
+        pc.lap(CK_FWD + min(tail, 63));
     }
     return true;
 }
@@ -423,14 +459,23 @@ __device__ bool dic_backward_thread(const SolveArgs& a, const Mat<T>& A, Vecs<T>
 {
     RowIter it = rows_of(g);
     Acc<T> acc;
-    for (int L = a.nlev - 1; L >= 0; L--) {
-        const int r0 = a.lvl[L], r1 = a.lvl[L + 1];
-        for (int p = r0 + it.first; p < r1; p += it.stride) {
-            T ww = v.w[p];
-            ww = row_chain<T, true, true>(ww, __ldg(A.Uptr + p), __ldg(A.Uptr + p + 1), A.Ucol, A.Uc, v.w);
-            v.w[p] = ww;
-            acc.prod(ww, v.r[p]);
+    const int tail = min(a.tail_from, a.nlev);
+    if (tail < a.nlev) {
+        if (g.bid == 0) {
+            for (int L = a.nlev - 1; L >= tail; L--) {
+                bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], (int)threadIdx.x, (int)blockDim.x, acc);
+                __syncthreads();
+            }
         }
+        if (tail == 0 && want_rho) {
+            double t[1] = {acc.value()};
+            block_reduce_store<1>(t, a.partials, SL_B, g.bid);
+        }
+        if (!group_sync(g)) return false;
+        pc.lap(CK_BWD + min(tail, 63));
+    }
+    for (int L = tail - 1; L >= 0; L--) {
+        bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], it.first, it.stride, acc);
         if (L == 0 && want_rho) {
             double t[1] = {acc.value()};
             block_reduce_store<1>(t, a.partials, SL_B, g.bid);
@@ -893,9 +938,9 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
 }
 
 template <int RM>
-__global__ void __launch_bounds__(256, RM ? 3 : 4) k_solve(SolveArgs a, unsigned long long timeout_ns)
+__global__ void __launch_bounds__(RM ? 256 : 1024, RM ? 3 : 1) k_solve(SolveArgs a, unsigned long long timeout_ns)
 {
-    Group g{a.bar, a.bar + 32, a.status, (int)gridDim.x, (int)blockIdx.x, timeout_ns};
+    Group g{reinterpret_cast<unsigned*>(a.status + DS_BARRIER), a.status, (int)gridDim.x, (int)blockIdx.x, timeout_ns};
     run_system<RM>(a, g);
 }
 
@@ -906,7 +951,8 @@ __global__ void __launch_bounds__(256, 3) k_solve_batch(BatchTable t, unsigned l
     while (s + 1 < t.n_sys && (int)blockIdx.x >= t.split[s + 1]) s++;
     if (threadIdx.x == 0) sa = *t.args[s];
     __syncthreads();
-    Group g{sa.bar, sa.bar + 32, sa.status, t.split[s + 1] - t.split[s], (int)blockIdx.x - t.split[s], timeout_ns};
+    Group g{reinterpret_cast<unsigned*>(sa.status + DS_BARRIER), sa.status, t.split[s + 1] - t.split[s],
+            (int)blockIdx.x - t.split[s], timeout_ns};
     run_system<0>(sa, g);
 }
 
@@ -953,6 +999,7 @@ SolveArgs make_args(spuma_ldu_t h)
     a.n = h->n;
     a.nf = h->nf;
     a.nlev = h->nlev;
+    a.tail_from = h->nlev;
     a.lvl = h->at<int>(L.lvl);
     a.perm = h->at<int>(L.perm);
     a.Lptr = h->at<int>(L.Lptr);
@@ -1025,10 +1072,24 @@ int default_threads(const spuma_solver_controls* ctl)
     return t;
 }
 
+// First level of the run of small last levels (each with at most `threads`
+// rows) that the solver's first block handles alone; SPUMA_TAIL_ROWS
+// overrides the row limit (0 disables).
+int tail_level(spuma_ldu_t h, int threads)
+{
+    int limit = threads;
+    if (const char* e = getenv("SPUMA_TAIL_ROWS")) limit = atoi(e);
+    int t = h->nlev;
+    while (t > 1 && (int64_t)h->h_lvl[t] - h->h_lvl[t - 1] <= limit) t--;
+    // keep at least two levels in the tail, else the single grid barrier saves nothing
+    return (h->nlev - t >= 2) ? t : h->nlev;
+}
+
 spuma_status launch_solve(spuma_ldu_t h, const SolveArgs& a, int threads, cudaStream_t s)
 {
-    if (threads < 32 || threads > 256 || threads % 32) {
-        set_error("block_threads must be a multiple of 32 in [32, 256]");
+    const int tmax = row_mode() ? 256 : 1024;
+    if (threads < 32 || threads > tmax || threads % 32) {
+        set_error("block_threads must be a multiple of 32 in [32, 256] (1024 for the thread-per-row kernel)");
         return SPUMA_ERR_INVALID_ARG;
     }
     int per_sm = solve_blocks_per_sm(threads, false);
@@ -1046,6 +1107,7 @@ spuma_status launch_solve(spuma_ldu_t h, const SolveArgs& a, int threads, cudaSt
     unsigned long long tns = barrier_timeout_ns();
     SolveArgs b = a;
     b.row_mode = row_mode();
+    b.tail_from = tail_level(h, threads);
     if (getenv("SPUMA_PHASE_CLOCKS")) {
         b.phase_clk = h->at<long long>(h->L.clk);
         SPUMA_CUDA(cudaMemsetAsync(b.phase_clk, 0, 8 * 256, s));
