@@ -38,13 +38,19 @@ __device__ __forceinline__ Mat<float> mat_of<float>(const SolveArgs& a)
 }
 
 // One row's multiply-add chain over entries [e0, e1) (DESC: from e1-1 down
-// to e0), taking the entries in groups of four: the column and coefficient
-// loads of a group are issued together, then its gathers, then the FMAs in
-// entry order -- two memory round trips per group instead of two per entry.
+// to e0), taking the entries in groups: the column and coefficient loads of a
+// group are issued together, then its gathers, then the FMAs in entry order --
+// two memory round trips per group instead of two per entry.  Group size 8 in
+// FP32, 6 in FP64 (a hex-mesh row has at most 6 entries).
+template <class T>
+struct ChainGroup {
+    static constexpr int G = sizeof(T) == 4 ? 8 : 6;
+};
+
 template <class T, bool DESC, bool NEG>
 __device__ __forceinline__ T row_chain(T acc, int e0, int e1, const int* col, const T* coef, const T* vec)
 {
-    constexpr int G = 4;
+    constexpr int G = ChainGroup<T>::G;
     for (int e = DESC ? e1 - 1 : e0; DESC ? e >= e0 : e < e1; e += DESC ? -G : G) {
         int c[G];
         T k[G], v[G];
@@ -64,13 +70,76 @@ __device__ __forceinline__ T row_chain(T acc, int e0, int e1, const int* col, co
     return acc;
 }
 
-// y_p = d_p x_p + lower entries (ascending face) + upper entries (ascending face)
+// Rows processed together by one thread (their loads are in flight at the
+// same time): two in FP32, one in FP64 (register budget).
+template <class T>
+struct RowsPerThread {
+    static constexpr int R = sizeof(T) == 4 ? 2 : 1;
+};
+
+// R rows' chains in lockstep: group g of every row is loaded, gathered and
+// applied together; each row still takes its entries in its own order.
+template <class T, int R, bool DESC, bool NEG>
+__device__ __forceinline__ void rows_chain(T (&acc)[R], const int (&e0)[R], const int (&e1)[R], const int* col,
+                                           const T* coef, const T* vec)
+{
+    constexpr int G = R == 1 ? ChainGroup<T>::G : 4;
+    for (int off = 0;; off += G) {
+        bool more = false;
+#pragma unroll
+        for (int k = 0; k < R; k++) more |= e0[k] + off < e1[k];
+        if (!more) break;
+        int c[R][G];
+        T cf[R][G], v[R][G];
+#pragma unroll
+        for (int k = 0; k < R; k++)
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+                const int ej = DESC ? e1[k] - 1 - off - j : e0[k] + off + j;
+                const bool ok = DESC ? ej >= e0[k] : ej < e1[k];
+                c[k][j] = ok ? __ldg(col + ej) : -1;
+                cf[k][j] = ok ? coef[ej] : T(0);
+            }
+#pragma unroll
+        for (int k = 0; k < R; k++)
+#pragma unroll
+            for (int j = 0; j < G; j++) v[k][j] = c[k][j] >= 0 ? vec[c[k][j]] : T(0);
+#pragma unroll
+        for (int k = 0; k < R; k++)
+#pragma unroll
+            for (int j = 0; j < G; j++)
+                if (c[k][j] >= 0) acc[k] = fmadd(NEG ? -cf[k][j] : cf[k][j], v[k][j], acc[k]);
+    }
+}
+
+// y_p = d_p x_p + lower entries (ascending face) + upper entries (ascending
+// face).  The row's lower and upper entries are taken as one list of
+// nL + nU entries, in groups, so both parts' loads are in flight together.
 template <class T>
 __device__ __forceinline__ T amul_row(const Mat<T>& A, const T* x, int p)
 {
+    constexpr int G = ChainGroup<T>::G;
+    const int l0 = __ldg(A.Lptr + p), nl = __ldg(A.Lptr + p + 1) - l0;
+    const int u0 = __ldg(A.Uptr + p), nt = nl + __ldg(A.Uptr + p + 1) - u0;
     T y = mul_rn(A.d[p], x[p]);
-    y = row_chain<T, false, false>(y, __ldg(A.Lptr + p), __ldg(A.Lptr + p + 1), A.Lcol, A.La, x);
-    y = row_chain<T, false, false>(y, __ldg(A.Uptr + p), __ldg(A.Uptr + p + 1), A.Ucol, A.Ua, x);
+    for (int k0 = 0; k0 < nt; k0 += G) {
+        int c[G];
+        T a[G], v[G];
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            const int k = k0 + j;
+            const bool low = k < nl;
+            const int e = low ? l0 + k : u0 + (k - nl);
+            const bool ok = k < nt;
+            c[j] = ok ? __ldg((low ? A.Lcol : A.Ucol) + e) : -1;
+            a[j] = ok ? (low ? A.La : A.Ua)[e] : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < G; j++) v[j] = c[j] >= 0 ? x[c[j]] : T(0);
+#pragma unroll
+        for (int j = 0; j < G; j++)
+            if (c[j] >= 0) y = fmadd(a[j], v[j], y);
+    }
     return y;
 }
 
@@ -394,17 +463,29 @@ template <class T>
 __device__ __forceinline__ void fwd_rows(const Mat<T>& A, Vecs<T> v, bool pending, T alpha, int r0, int r1, int first,
                                          int stride, Acc<T>& acc)
 {
-    for (int p = r0 + first; p < r1; p += stride) {
-        T rr = v.r[p];
-        if (pending) {
-            v.x[p] = fmadd(alpha, v.p[p], v.x[p]);
-            rr = fmadd(-alpha, v.q[p], rr);
-            v.r[p] = rr;
-            acc.add(fabs(rr));
+    constexpr int R = RowsPerThread<T>::R;
+    for (int pb = r0 + first; pb < r1; pb += R * stride) {
+        int p[R], e0[R], e1[R];
+        T ww[R];
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+            p[k] = pb + k * stride;
+            const bool ok = p[k] < r1;
+            e0[k] = ok ? __ldg(A.Lptr + p[k]) : 0;
+            e1[k] = ok ? __ldg(A.Lptr + p[k] + 1) : 0;
+            T rr = ok ? v.r[p[k]] : T(0);
+            if (pending && ok) {
+                v.x[p[k]] = fmadd(alpha, v.p[p[k]], v.x[p[k]]);
+                rr = fmadd(-alpha, v.q[p[k]], rr);
+                v.r[p[k]] = rr;
+                acc.add(fabs(rr));
+            }
+            ww[k] = ok ? mul_rn(A.rD[p[k]], rr) : T(0);
         }
-        T ww = mul_rn(A.rD[p], rr);
-        ww = row_chain<T, false, true>(ww, __ldg(A.Lptr + p), __ldg(A.Lptr + p + 1), A.Lcol, A.Lc, v.w);
-        v.w[p] = ww;
+        rows_chain<T, R, false, true>(ww, e0, e1, A.Lcol, A.Lc, v.w);
+#pragma unroll
+        for (int k = 0; k < R; k++)
+            if (p[k] < r1) v.w[p[k]] = ww[k];
     }
 }
 
@@ -412,11 +493,25 @@ template <class T>
 __device__ __forceinline__ void bwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int r1, int first, int stride,
                                          Acc<T>& acc)
 {
-    for (int p = r0 + first; p < r1; p += stride) {
-        T ww = v.w[p];
-        ww = row_chain<T, true, true>(ww, __ldg(A.Uptr + p), __ldg(A.Uptr + p + 1), A.Ucol, A.Uc, v.w);
-        v.w[p] = ww;
-        acc.prod(ww, v.r[p]);
+    constexpr int R = RowsPerThread<T>::R;
+    for (int pb = r0 + first; pb < r1; pb += R * stride) {
+        int p[R], e0[R], e1[R];
+        T ww[R];
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+            p[k] = pb + k * stride;
+            const bool ok = p[k] < r1;
+            e0[k] = ok ? __ldg(A.Uptr + p[k]) : 0;
+            e1[k] = ok ? __ldg(A.Uptr + p[k] + 1) : 0;
+            ww[k] = ok ? v.w[p[k]] : T(0);
+        }
+        rows_chain<T, R, true, true>(ww, e0, e1, A.Ucol, A.Uc, v.w);
+#pragma unroll
+        for (int k = 0; k < R; k++)
+            if (p[k] < r1) {
+                v.w[p[k]] = ww[k];
+                acc.prod(ww[k], v.r[p[k]]);
+            }
     }
 }
 
@@ -502,6 +597,43 @@ __device__ __forceinline__ bool dic_backward(const SolveArgs& a, const Mat<T>& A
     return dic_backward_thread<T>(a, A, v, want_rho, g, pc);
 }
 
+// 16-byte vector of the working precision (float4 / double2): the streaming
+// passes move 16 bytes per load so that enough bytes are in flight per SM.
+template <class T>
+struct V16;
+template <>
+struct V16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+};
+template <>
+struct V16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+};
+// component-wise a*x + y and sum|x| on the vector types (register-only)
+__device__ __forceinline__ float4 vfma(float a, float4 x, float4 y)
+{
+    return make_float4(__fmaf_rn(a, x.x, y.x), __fmaf_rn(a, x.y, y.y), __fmaf_rn(a, x.z, y.z), __fmaf_rn(a, x.w, y.w));
+}
+__device__ __forceinline__ double2 vfma(double a, double2 x, double2 y)
+{
+    return make_double2(__fma_rn(a, x.x, y.x), __fma_rn(a, x.y, y.y));
+}
+template <class A>
+__device__ __forceinline__ void vadd_abs(A& acc, float4 r)
+{
+    acc.add(fabsf(r.x));
+    acc.add(fabsf(r.y));
+    acc.add(fabsf(r.z));
+    acc.add(fabsf(r.w));
+}
+template <class A>
+__device__ __forceinline__ void vadd_abs(A& acc, double2 r)
+{
+    acc.add(fabs(r.x));
+    acc.add(fabs(r.y));
+}
 // Diagonal / no preconditioning in one pass, fused with the pending x/r
 // update; returns sum|r| (of the updated r) and rho = w.r through t[0], t[1].
 template <class T>
@@ -529,12 +661,36 @@ __device__ bool diag_pass(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool p
     return true;
 }
 
-// p = w (first) or w + beta p
+// p = w (first) or w + beta p; 16-byte loads, scalar tail
 template <class T>
 __device__ bool search_direction(const SolveArgs& a, Vecs<T> v, bool first, T beta, const Group& g)
 {
+    using VT = typename V16<T>::type;
+    constexpr int W = V16<T>::n;
     RowIter it = rows_of(g);
-    for (int p = it.first; p < a.n; p += it.stride) v.p[p] = first ? v.w[p] : fmadd(beta, v.p[p], v.w[p]);
+    const int nv = a.n / W;
+    VT* pv = reinterpret_cast<VT*>(v.p);
+    const VT* wv = reinterpret_cast<const VT*>(v.w);
+    constexpr int R = 1;
+    for (int ib = it.first; ib < nv; ib += R * it.stride) {
+        VT pp[R], ww[R];
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+            const int i = ib + k * it.stride;
+            if (i < nv) {
+                ww[k] = wv[i];
+                if (!first) pp[k] = pv[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+            const int i = ib + k * it.stride;
+            if (i < nv) {
+                pv[i] = first ? ww[k] : vfma(beta, pp[k], ww[k]);
+            }
+        }
+    }
+    for (int p = nv * W + it.first; p < a.n; p += it.stride) v.p[p] = first ? v.w[p] : fmadd(beta, v.p[p], v.w[p]);
     return group_sync(g);
 }
 
@@ -555,10 +711,56 @@ __device__ bool amul_sigma(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const
         }
     } else {
         RowIter it = rows_of(g);
-        for (int p = it.first; p < a.n; p += it.stride) {
-            const T qq = amul_row<T>(A, v.p, p);
-            v.q[p] = qq;
-            asig.prod(qq, v.p[p]);
+        constexpr int R = RowsPerThread<T>::R;
+        constexpr int G = R == 1 ? ChainGroup<T>::G : 4;
+        for (int pb = it.first; pb < a.n; pb += R * it.stride) {
+            int p[R], l0[R], nl[R], u0[R], nt[R];
+            T y[R], pp[R];
+#pragma unroll
+            for (int k = 0; k < R; k++) {
+                p[k] = pb + k * it.stride;
+                const bool ok = p[k] < a.n;
+                l0[k] = ok ? __ldg(A.Lptr + p[k]) : 0;
+                nl[k] = ok ? __ldg(A.Lptr + p[k] + 1) - l0[k] : 0;
+                u0[k] = ok ? __ldg(A.Uptr + p[k]) : 0;
+                nt[k] = ok ? nl[k] + __ldg(A.Uptr + p[k] + 1) - u0[k] : 0;
+                pp[k] = ok ? v.p[p[k]] : T(0);
+                y[k] = ok ? mul_rn(A.d[p[k]], pp[k]) : T(0);
+            }
+            for (int off = 0;; off += G) {
+                bool more = false;
+#pragma unroll
+                for (int k = 0; k < R; k++) more |= off < nt[k];
+                if (!more) break;
+                int c[R][G];
+                T cf[R][G], vv[R][G];
+#pragma unroll
+                for (int k = 0; k < R; k++)
+#pragma unroll
+                    for (int j = 0; j < G; j++) {
+                        const int kk = off + j;
+                        const bool low = kk < nl[k];
+                        const int e = low ? l0[k] + kk : u0[k] + (kk - nl[k]);
+                        const bool ok = kk < nt[k];
+                        c[k][j] = ok ? __ldg((low ? A.Lcol : A.Ucol) + e) : -1;
+                        cf[k][j] = ok ? (low ? A.La : A.Ua)[e] : T(0);
+                    }
+#pragma unroll
+                for (int k = 0; k < R; k++)
+#pragma unroll
+                    for (int j = 0; j < G; j++) vv[k][j] = c[k][j] >= 0 ? v.p[c[k][j]] : T(0);
+#pragma unroll
+                for (int k = 0; k < R; k++)
+#pragma unroll
+                    for (int j = 0; j < G; j++)
+                        if (c[k][j] >= 0) y[k] = fmadd(cf[k][j], vv[k][j], y[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < R; k++)
+                if (p[k] < a.n) {
+                    v.q[p[k]] = y[k];
+                    asig.prod(y[k], pp[k]);
+                }
         }
     }
     double sacc[1] = {asig.value()};
@@ -567,6 +769,59 @@ __device__ bool amul_sigma(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const
     double sg[1];
     grid_reduce_read<1>(sg, a.partials, SL_C, g.nblocks);
     *sigma = sg[0];
+    return true;
+}
+
+// x += alpha p, r -= alpha q and sum|r| as a pass of its own (when the update
+// is not fused into the forward sweep); 16-byte loads, scalar tail.
+template <class T>
+__device__ bool update_pass(const SolveArgs& a, Vecs<T> v, T alpha, const Group& g, double* ressum)
+{
+    using VT = typename V16<T>::type;
+    constexpr int W = V16<T>::n;
+    RowIter it = rows_of(g);
+    Acc<T> acc;
+    const int nv = a.n / W;
+    VT* xv = reinterpret_cast<VT*>(v.x);
+    VT* rv = reinterpret_cast<VT*>(v.r);
+    const VT* pv = reinterpret_cast<const VT*>(v.p);
+    const VT* qv = reinterpret_cast<const VT*>(v.q);
+    constexpr int R = 1;
+    for (int ib = it.first; ib < nv; ib += R * it.stride) {
+        VT xx[R], pp[R], qq[R], rr[R];
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+            const int i = ib + k * it.stride;
+            if (i < nv) {
+                xx[k] = xv[i];
+                pp[k] = pv[i];
+                qq[k] = qv[i];
+                rr[k] = rv[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+            const int i = ib + k * it.stride;
+            if (i < nv) {
+                xx[k] = vfma(alpha, pp[k], xx[k]);
+                rr[k] = vfma(-alpha, qq[k], rr[k]);
+                vadd_abs(acc, rr[k]);
+                xv[i] = xx[k];
+                rv[i] = rr[k];
+            }
+        }
+    }
+    for (int p = nv * W + it.first; p < a.n; p += it.stride) {
+        v.x[p] = fmadd(alpha, v.p[p], v.x[p]);
+        const T r1 = fmadd(-alpha, v.q[p], v.r[p]);
+        v.r[p] = r1;
+        acc.add(fabs(r1));
+    }
+    double t[1] = {acc.value()};
+    block_reduce_store<1>(t, a.partials, SL_A, g.bid);
+    if (!group_sync(g)) return false;
+    grid_reduce_read<1>(t, a.partials, SL_A, g.nblocks);
+    *ressum = t[0];
     return true;
 }
 
@@ -580,15 +835,23 @@ __device__ int precondition(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool
 {
     double ressum = 0.0;
     if (a.precond == SPUMA_PRECOND_DIC) {
-        if (!dic_forward<T, RM>(a, A, v, pending, alpha, g, pc)) return -1;
-        if (pending) {
-            double t[1];
-            grid_reduce_read<1>(t, a.partials, SL_A, g.nblocks);
-            ressum = t[0];
+        if (pending && !a.fuse_update) {
+            if (!update_pass<T>(a, v, alpha, g, &ressum)) return -1;
+            pc.lap(CK_CORR);
+            const int act = after_fwd(ressum);
+            if (act == 1 || act < 0) return act;
+            if (!dic_forward<T, RM>(a, A, v, false, T(0), g, pc)) return -1;
+        } else {
+            if (!dic_forward<T, RM>(a, A, v, pending, alpha, g, pc)) return -1;
+            if (pending) {
+                double t[1];
+                grid_reduce_read<1>(t, a.partials, SL_A, g.nblocks);
+                ressum = t[0];
+            }
+            const int act = after_fwd(ressum);       // 0 continue, 1 stop, 2 redo (r replaced), -1 error
+            if (act == 1 || act < 0) return act;
+            if (act == 2 && !dic_forward<T, RM>(a, A, v, false, T(0), g, pc)) return -1;
         }
-        const int act = after_fwd(ressum);       // 0 continue, 1 stop, 2 redo (r replaced), -1 error
-        if (act == 1 || act < 0) return act;
-        if (act == 2 && !dic_forward<T, RM>(a, A, v, false, T(0), g, pc)) return -1;
         if (!dic_backward<T, RM>(a, A, v, true, g, pc)) return -1;
         double t[1];
         grid_reduce_read<1>(t, a.partials, SL_B, g.nblocks);
@@ -1048,6 +1311,15 @@ static int row_mode()
     return m;
 }
 
+static int fuse_update_default()
+{
+    static int m = [] {
+        const char* e = getenv("SPUMA_FUSE_UPDATE");
+        return e && atoi(e) == 1 ? 1 : 0;
+    }();
+    return m;
+}
+
 static std::mutex g_occ_mu;
 static std::map<int, int> g_occ;   // (kernel, block threads) -> co-resident blocks per SM
 
@@ -1068,8 +1340,8 @@ int solve_blocks_per_sm(int threads, bool batch)
 
 int default_threads(const spuma_solver_controls* ctl)
 {
-    int t = ctl && ctl->block_threads > 0 ? ctl->block_threads : 256;
-    return t;
+    if (ctl && ctl->block_threads > 0) return ctl->block_threads;
+    return row_mode() ? 256 : 1024;
 }
 
 // First level of the run of small last levels (each with at most `threads`
@@ -1108,6 +1380,9 @@ spuma_status launch_solve(spuma_ldu_t h, const SolveArgs& a, int threads, cudaSt
     SolveArgs b = a;
     b.row_mode = row_mode();
     b.tail_from = tail_level(h, threads);
+    // SPUMA_FUSE_UPDATE=1 fuses the x/r update into the forward DIC sweep
+    // (default: a pass of its own ahead of the sweep)
+    b.fuse_update = fuse_update_default();
     if (getenv("SPUMA_PHASE_CLOCKS")) {
         b.phase_clk = h->at<long long>(h->L.clk);
         SPUMA_CUDA(cudaMemsetAsync(b.phase_clk, 0, 8 * 256, s));

@@ -41,9 +41,11 @@ def test_device_errors_are_reported_not_trapped():
         M.solve(dev(do), dev(uo), dev(b), None, SolverControls(precond=2))
     assert e.value.status == 7
     # a grid barrier whose wait runs out returns a status instead of hanging
+    # (32-thread blocks: the 512-cell mesh spans 16 blocks, so blocks do wait)
     lib().spuma_set_barrier_timeout_ns(0)
     try:
-        _, p = M.solve(dev(do), dev(uo), dev(c.b), None, SolverControls(precond=2), check_status=False)
+        _, p = M.solve(dev(do), dev(uo), dev(c.b), None, SolverControls(precond=2, block_threads=32),
+                       check_status=False)
     finally:
         lib().spuma_set_barrier_timeout_ns(2_000_000_000)
     assert p["status"] == 8 and p["converged"] == 0
