@@ -19,8 +19,9 @@ namespace spuma {
 SolveArgs make_args(spuma_ldu_t h);
 void fill_controls(SolveArgs& a, const spuma_solver_controls* ctl);
 bool ctl_ok(const spuma_solver_controls* c);
-int solve_blocks_per_sm(int threads, bool batch);
-spuma_status launch_batch_kernel(const BatchTable& t, int grid, int threads, cudaStream_t s);
+int solve_blocks_per_sm(int threads, bool batch, int kind);
+int batch_kind(int precision);
+spuma_status launch_batch_kernel(const BatchTable& t, int grid, int threads, int kind, cudaStream_t s);
 
 // Split `grid` blocks between systems in proportion to their weights, at
 // least one block each (largest-remainder rounding; deterministic).
@@ -129,7 +130,7 @@ struct spuma_batch {
     int n_sys = 0;
     std::vector<spuma_ldu_t> hs;
     std::vector<SolveArgs> args;
-    int threads = 256, policy = 1, grid = 0;
+    int threads = 256, policy = 1, grid = 0, kind = 1;
     double tuned_ms = -1.0;
     BatchTable table{};
     cudaGraph_t graph = nullptr;
@@ -138,7 +139,7 @@ struct spuma_batch {
 
 static spuma_status batch_configure(spuma_batch* bt, int threads, int policy, int num_sms)
 {
-    int per_sm = solve_blocks_per_sm(threads, true);
+    int per_sm = solve_blocks_per_sm(threads, true, bt->kind);
     if (per_sm < 1) { set_error("batch kernel cannot be resident"); return SPUMA_ERR_CUDA; }
     int grid = std::min(per_sm * num_sms, kMaxBlocks);
     if (grid < bt->n_sys) { set_error("more systems than co-resident blocks"); return SPUMA_ERR_INVALID_ARG; }
@@ -159,7 +160,7 @@ static spuma_status batch_launch(spuma_batch* bt, cudaStream_t s, bool count = t
         spuma_ldu_t h = bt->hs[k];
         SPUMA_CUDA(cudaMemsetAsync(h->at<char>(h->L.bar), 0, h->L.status + 256 - h->L.bar, s));
     }
-    spuma_status st = launch_batch_kernel(bt->table, bt->grid, bt->threads, s);
+    spuma_status st = launch_batch_kernel(bt->table, bt->grid, bt->threads, bt->kind, s);
     if (st == SPUMA_OK && count) count_launch();
     return st;
 }
@@ -206,6 +207,7 @@ spuma_status spuma_batch_create(int32_t n_sys, const spuma_ldu_t* hs, const doub
     cudaStream_t s = (cudaStream_t)stream;
     spuma_batch* bt = new spuma_batch();
     bt->n_sys = n_sys;
+    bt->kind = batch_kind(ctl->precision);
     bt->hs.assign(hs, hs + n_sys);
     bt->args.resize(n_sys);
     auto fail = [&](spuma_status st) {

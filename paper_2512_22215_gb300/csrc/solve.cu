@@ -1,17 +1,25 @@
-// solve.cu -- the persistent PCG solver (FP64 and mixed FP32/FP64 iterative
-// refinement), the level-scheduled DIC factor and sweeps, the prepared-matrix
-// Amul, and their host entry points.
+// solve.cu -- the persistent PCG solver (FP64, and mixed FP32/FP64 by reliable
+// updates or restarted refinement), the level-scheduled DIC factor and sweeps,
+// the prepared-matrix Amul, and their host entry points.
 //
 // One cooperative launch per solve.  Rows live in the handle's level order:
 // level L (rows whose longest chain of lower neighbours has length L) is the
 // contiguous range lvl[L]..lvl[L+1], and every row keeps its neighbour-side
 // ("lower") and owner-side ("upper") entries in ascending face order, so each
 // row sum is taken in exactly the order of the sequential face loop.
+//
+// One PCG iteration with DIC (grid barriers after each step, and after each
+// DIC level inside the sweeps):
+//   update pass       x += alpha p, r -= alpha q, sum|r|       -> converged?
+//   forward sweep     w = (P + L)^-1 r, level by level
+//   backward sweep    w = (P + U)^-1 P w, rho = w.r            -> beta
+//   search direction  p = w + beta p
+//   Amul              q = A p, sigma = q.p                     -> alpha
 #include <algorithm>
-#include <cstdlib>
 #include <cmath>
-#include <mutex>
+#include <cstdlib>
 #include <map>
+#include <mutex>
 
 #include "solve.cuh"
 
@@ -37,53 +45,23 @@ __device__ __forceinline__ Mat<float> mat_of<float>(const SolveArgs& a)
     return Mat<float>{a.Lptr, a.Lcol, a.La32, a.Lc32, a.Uptr, a.Ucol, a.Ua32, a.Uc32, a.d32, a.rD32};
 }
 
-// One row's multiply-add chain over entries [e0, e1) (DESC: from e1-1 down
-// to e0), taking the entries in groups: the column and coefficient loads of a
-// group are issued together, then its gathers, then the FMAs in entry order --
-// two memory round trips per group instead of two per entry.  Group size 8 in
-// FP32, 6 in FP64 (a hex-mesh row has at most 6 entries).
+// Group sizes of the row chains: a row's entries are taken in groups whose
+// column and coefficient loads are issued together, then the gathers, then
+// the FMAs in entry order (two memory round trips per group, not per entry).
+// FP64 rows run one per thread with groups of 6 (a hex-mesh row has at most
+// 6 entries); FP32 rows run two per thread in lockstep with groups of 4.
 template <class T>
-struct ChainGroup {
-    static constexpr int G = sizeof(T) == 4 ? 8 : 6;
-};
-
-template <class T, bool DESC, bool NEG>
-__device__ __forceinline__ T row_chain(T acc, int e0, int e1, const int* col, const T* coef, const T* vec)
-{
-    constexpr int G = ChainGroup<T>::G;
-    for (int e = DESC ? e1 - 1 : e0; DESC ? e >= e0 : e < e1; e += DESC ? -G : G) {
-        int c[G];
-        T k[G], v[G];
-#pragma unroll
-        for (int j = 0; j < G; j++) {
-            const int ej = DESC ? e - j : e + j;
-            const bool ok = DESC ? ej >= e0 : ej < e1;
-            c[j] = ok ? __ldg(col + ej) : -1;
-            k[j] = ok ? coef[ej] : T(0);
-        }
-#pragma unroll
-        for (int j = 0; j < G; j++) v[j] = c[j] >= 0 ? vec[c[j]] : T(0);
-#pragma unroll
-        for (int j = 0; j < G; j++)
-            if (c[j] >= 0) acc = fmadd(NEG ? -k[j] : k[j], v[j], acc);
-    }
-    return acc;
-}
-
-// Rows processed together by one thread (their loads are in flight at the
-// same time): two in FP32, one in FP64 (register budget).
-template <class T>
-struct RowsPerThread {
+struct ChainShape {
     static constexpr int R = sizeof(T) == 4 ? 2 : 1;
+    static constexpr int G = sizeof(T) == 4 ? 4 : 6;
 };
 
-// R rows' chains in lockstep: group g of every row is loaded, gathered and
-// applied together; each row still takes its entries in its own order.
-template <class T, int R, bool DESC, bool NEG>
+// R rows' chains in lockstep; each row takes its entries [e0, e1) in its own
+// order (DESC: from e1-1 down to e0).
+template <class T, int R, int G, bool DESC, bool NEG>
 __device__ __forceinline__ void rows_chain(T (&acc)[R], const int (&e0)[R], const int (&e1)[R], const int* col,
                                            const T* coef, const T* vec)
 {
-    constexpr int G = R == 1 ? ChainGroup<T>::G : 4;
     for (int off = 0;; off += G) {
         bool more = false;
 #pragma unroll
@@ -112,35 +90,60 @@ __device__ __forceinline__ void rows_chain(T (&acc)[R], const int (&e0)[R], cons
     }
 }
 
-// y_p = d_p x_p + lower entries (ascending face) + upper entries (ascending
-// face).  The row's lower and upper entries are taken as one list of
-// nL + nU entries, in groups, so both parts' loads are in flight together.
+// y = A x for R rows: d_p x_p, then the row's lower entries (ascending face)
+// and upper entries (ascending face) taken as one list of nL + nU entries.
+template <class T, int R, int G>
+__device__ __forceinline__ void amul_rows(const Mat<T>& A, const T* x, const int (&p)[R], int n, T (&y)[R],
+                                          T (&xp)[R])
+{
+    int l0[R], nl[R], u0[R], nt[R];
+#pragma unroll
+    for (int k = 0; k < R; k++) {
+        const bool ok = p[k] < n;
+        l0[k] = ok ? __ldg(A.Lptr + p[k]) : 0;
+        nl[k] = ok ? __ldg(A.Lptr + p[k] + 1) - l0[k] : 0;
+        u0[k] = ok ? __ldg(A.Uptr + p[k]) : 0;
+        nt[k] = ok ? nl[k] + __ldg(A.Uptr + p[k] + 1) - u0[k] : 0;
+        xp[k] = ok ? x[p[k]] : T(0);
+        y[k] = ok ? mul_rn(A.d[p[k]], xp[k]) : T(0);
+    }
+    for (int off = 0;; off += G) {
+        bool more = false;
+#pragma unroll
+        for (int k = 0; k < R; k++) more |= off < nt[k];
+        if (!more) break;
+        int c[R][G];
+        T cf[R][G], vv[R][G];
+#pragma unroll
+        for (int k = 0; k < R; k++)
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+                const int kk = off + j;
+                const bool low = kk < nl[k];
+                const int e = low ? l0[k] + kk : u0[k] + (kk - nl[k]);
+                const bool ok = kk < nt[k];
+                c[k][j] = ok ? __ldg((low ? A.Lcol : A.Ucol) + e) : -1;
+                cf[k][j] = ok ? (low ? A.La : A.Ua)[e] : T(0);
+            }
+#pragma unroll
+        for (int k = 0; k < R; k++)
+#pragma unroll
+            for (int j = 0; j < G; j++) vv[k][j] = c[k][j] >= 0 ? x[c[k][j]] : T(0);
+#pragma unroll
+        for (int k = 0; k < R; k++)
+#pragma unroll
+            for (int j = 0; j < G; j++)
+                if (c[k][j] >= 0) y[k] = fmadd(cf[k][j], vv[k][j], y[k]);
+    }
+}
+
 template <class T>
 __device__ __forceinline__ T amul_row(const Mat<T>& A, const T* x, int p)
 {
-    constexpr int G = ChainGroup<T>::G;
-    const int l0 = __ldg(A.Lptr + p), nl = __ldg(A.Lptr + p + 1) - l0;
-    const int u0 = __ldg(A.Uptr + p), nt = nl + __ldg(A.Uptr + p + 1) - u0;
-    T y = mul_rn(A.d[p], x[p]);
-    for (int k0 = 0; k0 < nt; k0 += G) {
-        int c[G];
-        T a[G], v[G];
-#pragma unroll
-        for (int j = 0; j < G; j++) {
-            const int k = k0 + j;
-            const bool low = k < nl;
-            const int e = low ? l0 + k : u0 + (k - nl);
-            const bool ok = k < nt;
-            c[j] = ok ? __ldg((low ? A.Lcol : A.Ucol) + e) : -1;
-            a[j] = ok ? (low ? A.La : A.Ua)[e] : T(0);
-        }
-#pragma unroll
-        for (int j = 0; j < G; j++) v[j] = c[j] >= 0 ? x[c[j]] : T(0);
-#pragma unroll
-        for (int j = 0; j < G; j++)
-            if (c[j] >= 0) y = fmadd(a[j], v[j], y);
-    }
-    return y;
+    int pp[1] = {p};
+    T y[1], xp[1];
+    amul_rows<T, 1, ChainShape<T>::G>(A, x, pp, p + 1, y, xp);
+    return y[0];
 }
 
 template <class T>
@@ -157,23 +160,13 @@ __device__ __forceinline__ RowIter rows_of(const Group& g)
     return RowIter{g.bid * (int)blockDim.x + (int)threadIdx.x, g.nblocks * (int)blockDim.x};
 }
 
-struct WarpIter {
-    int first, stride, lane;
-};
-
-__device__ __forceinline__ WarpIter warps_of(const Group& g)
-{
-    const int t = g.bid * (int)blockDim.x + (int)threadIdx.x;
-    return WarpIter{t >> 5, (g.nblocks * (int)blockDim.x) >> 5, (int)threadIdx.x & 31};
-}
-
 // Optional phase timing: group block 0, thread 0 adds SM-clock deltas between
 // consecutive marks into phase_clk[slot] (slots: 0..63 forward level, 64..127
 // backward level, 128 search direction, 129 Amul + sigma, 130 diagonal pass,
-// 131 init, 132 outer residual, 133 inner init, 134 correction, 135 gather,
-// 136 factor, 140 iterations).
-enum ClkSlot { CK_FWD = 0, CK_BWD = 64, CK_PUPD = 128, CK_AMUL = 129, CK_DIAG = 130, CK_INIT = 131, CK_RESID = 132,
-               CK_INNER0 = 133, CK_CORR = 134, CK_GATHER = 135, CK_FACTOR = 136, CK_ITERS = 140 };
+// 132 FP64 refinement residual, 134 update pass, 140 iterations).
+enum ClkSlot { CK_FWD = 0, CK_BWD = 64, CK_PUPD = 128, CK_AMUL = 129, CK_DIAG = 130, CK_RESID = 132,
+               CK_UPD = 134, CK_ITERS = 140 };
+
 __device__ __forceinline__ long long sm_clock()
 {
     long long t;
@@ -236,84 +229,42 @@ struct Acc<float> {
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
-// Warp-cooperative row chains.  A warp owns 32 consecutive rows whose entries
-// [cb0, ce0) are contiguous; it loads them coalesced, issues every gather of
-// the chunk at once, stages (coefficient, gathered value) pairs in shared
-// memory, and each lane then runs its own row's multiply-add chain in entry
-// order (DESC: descending), exactly as the sequential face loop would.
-constexpr int kSub = 128;        // staged entries per warp and sub-chunk
-constexpr int kMaxWarps = 8;     // 256 threads per block
-__shared__ __align__(16) unsigned char g_stage[kMaxWarps * kSub * 16];
-
-template <class T, bool DESC, bool NEG>
-__device__ __forceinline__ T warp_chain(T acc, int eb, int ee, int cb0, int ce0, const int* col, const T* coef,
-                                        const T* vec, int lane)
-{
-    if (ce0 <= cb0) return acc;
-    T* sc = reinterpret_cast<T*>(g_stage) + (threadIdx.x >> 5) * (2 * kSub);
-    T* sv = sc + kSub;
-    const int nsub = (ce0 - cb0 + kSub - 1) / kSub;
-    for (int si = 0; si < nsub; si++) {
-        const int base = cb0 + (DESC ? nsub - 1 - si : si) * kSub;
-        const int lim = min(ce0, base + kSub);
-        int ci[kSub / 32];
-        T cv[kSub / 32];
-#pragma unroll
-        for (int k = 0; k < kSub / 32; k++) {
-            const int e = base + lane + 32 * k;
-            ci[k] = e < lim ? __ldg(col + e) : -1;
-            cv[k] = e < lim ? coef[e] : T(0);
-        }
-        T gv[kSub / 32];
-#pragma unroll
-        for (int k = 0; k < kSub / 32; k++) gv[k] = ci[k] >= 0 ? vec[ci[k]] : T(0);
-#pragma unroll
-        for (int k = 0; k < kSub / 32; k++) {
-            const int o = lane + 32 * k;
-            if (base + o < lim) {
-                sc[o] = cv[k];
-                sv[o] = gv[k];
-            }
-        }
-        __syncwarp();
-        const int lo = max(eb, base) - base, hi = min(ee, lim) - base;
-        if (DESC) {
-            for (int o = hi - 1; o >= lo; o--) acc = fmadd(NEG ? -sc[o] : sc[o], sv[o], acc);
-        } else {
-            for (int o = lo; o < hi; o++) acc = fmadd(NEG ? -sc[o] : sc[o], sv[o], acc);
-        }
-        __syncwarp();
-    }
-    return acc;
-}
-
-// Entry range of the lane's row and of the warp's chunk of rows [p0, p0+nv).
-__device__ __forceinline__ void chunk_range(const int* ptr, int p0, int nv, int lane, int& eb, int& ee, int& cb0,
-                                            int& ce0)
-{
-    const bool v = lane < nv;
-    eb = v ? __ldg(ptr + p0 + lane) : 0;
-    ee = v ? __ldg(ptr + p0 + lane + 1) : 0;
-    cb0 = __shfl_sync(0xffffffffu, eb, 0);
-    ce0 = __shfl_sync(0xffffffffu, ee, nv - 1);
-}
-
-// y_p = d_p x_p + lower entries (ascending face) + upper entries (ascending
-// face), warp-cooperative; valid lanes return y for row p0 + lane.
+// 16-byte vector of the working precision (float4 / double2): the streaming
+// passes move 16 bytes per load so that enough bytes are in flight per SM.
 template <class T>
-__device__ __forceinline__ T warp_amul_row(const Mat<T>& A, const T* x, int p0, int nv, int lane)
+struct V16;
+template <>
+struct V16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+};
+template <>
+struct V16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+};
+__device__ __forceinline__ float4 vfma(float a, float4 x, float4 y)
 {
-    const int p = p0 + lane;
-    const bool v = lane < nv;
-    T y = v ? mul_rn(A.d[p], x[p]) : T(0);
-    int eb, ee, cb0, ce0;
-    chunk_range(A.Lptr, p0, nv, lane, eb, ee, cb0, ce0);
-    y = warp_chain<T, false, false>(y, eb, ee, cb0, ce0, A.Lcol, A.La, x, lane);
-    chunk_range(A.Uptr, p0, nv, lane, eb, ee, cb0, ce0);
-    y = warp_chain<T, false, false>(y, eb, ee, cb0, ce0, A.Ucol, A.Ua, x, lane);
-    return y;
+    return make_float4(__fmaf_rn(a, x.x, y.x), __fmaf_rn(a, x.y, y.y), __fmaf_rn(a, x.z, y.z), __fmaf_rn(a, x.w, y.w));
 }
-
+__device__ __forceinline__ double2 vfma(double a, double2 x, double2 y)
+{
+    return make_double2(__fma_rn(a, x.x, y.x), __fma_rn(a, x.y, y.y));
+}
+template <class A>
+__device__ __forceinline__ void vadd_abs(A& acc, float4 r)
+{
+    acc.add(fabsf(r.x));
+    acc.add(fabsf(r.y));
+    acc.add(fabsf(r.z));
+    acc.add(fabsf(r.w));
+}
+template <class A>
+__device__ __forceinline__ void vadd_abs(A& acc, double2 r)
+{
+    acc.add(fabs(r.x));
+    acc.add(fabs(r.y));
+}
 // ------------------------------------------------------------ phases --------
 // Gather the LDU coefficients into the internal layout (+ FP32 copies).
 __device__ bool phase_gather(const SolveArgs& a, const Group& g)
@@ -362,12 +313,13 @@ __device__ bool phase_factor(const SolveArgs& a, const Group& g)
     }
     for (int p = it.first; p < a.n; p += it.stride) {
         double rd;
-        if (a.precond == SPUMA_PRECOND_DIC)
+        if (a.precond == SPUMA_PRECOND_DIC) {
             rd = __ddiv_rn(1.0, a.rD64[p]);
-        else if (a.precond == SPUMA_PRECOND_DIAGONAL)
+        } else if (a.precond == SPUMA_PRECOND_DIAGONAL) {
             rd = __ddiv_rn(1.0, a.d64[p]);
-        else
+        } else {
             rd = 1.0;
+        }
         a.rD64[p] = rd;
         a.rD32[p] = (float)rd;
         if (a.precond == SPUMA_PRECOND_DIC) {
@@ -386,84 +338,14 @@ __device__ bool phase_factor(const SolveArgs& a, const Group& g)
     return group_sync(g);
 }
 
-// DIC forward sweep over all levels, optionally fused with the pending
-// x/r update of the previous PCG iteration (x += alpha p, r -= alpha q) and
-// the sum|r| of the updated residual (slot A).
-template <class T>
-__device__ bool dic_forward_warp(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool pending, T alpha, const Group& g,
-                                 PhaseClock& pc)
-{
-    const WarpIter wi = warps_of(g);
-    Acc<T> acc;
-    for (int L = 0; L < a.nlev; L++) {
-        const int r0 = a.lvl[L], r1 = a.lvl[L + 1];
-        for (int p0 = r0 + 32 * wi.first; p0 < r1; p0 += 32 * wi.stride) {
-            const int nv = min(32, r1 - p0), p = p0 + wi.lane;
-            const bool ok = wi.lane < nv;
-            T rr = ok ? v.r[p] : T(0);
-            if (pending && ok) {
-                v.x[p] = fmadd(alpha, v.p[p], v.x[p]);
-                rr = fmadd(-alpha, v.q[p], rr);
-                v.r[p] = rr;
-                acc.add(fabs(rr));
-            }
-            T ww = ok ? mul_rn(A.rD[p], rr) : T(0);
-            int eb, ee, cb0, ce0;
-            chunk_range(A.Lptr, p0, nv, wi.lane, eb, ee, cb0, ce0);
-            ww = warp_chain<T, false, true>(ww, eb, ee, cb0, ce0, A.Lcol, A.Lc, v.w, wi.lane);
-            if (ok) v.w[p] = ww;
-        }
-        if (L == a.nlev - 1 && pending) {
-            double t[1] = {acc.value()};
-            block_reduce_store<1>(t, a.partials, SL_A, g.bid);
-        }
-        if (!group_sync(g)) return false;
-        pc.lap(CK_FWD + min(L, 63));
-    }
-    return true;
-}
-
-// DIC backward sweep (levels descending, upper entries descending face order),
-// with rho = sum w r into slot B.
-template <class T>
-__device__ bool dic_backward_warp(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool want_rho, const Group& g,
-                                  PhaseClock& pc)
-{
-    const WarpIter wi = warps_of(g);
-    Acc<T> acc;
-    for (int L = a.nlev - 1; L >= 0; L--) {
-        const int r0 = a.lvl[L], r1 = a.lvl[L + 1];
-        for (int p0 = r0 + 32 * wi.first; p0 < r1; p0 += 32 * wi.stride) {
-            const int nv = min(32, r1 - p0), p = p0 + wi.lane;
-            const bool ok = wi.lane < nv;
-            T ww = ok ? v.w[p] : T(0);
-            int eb, ee, cb0, ce0;
-            chunk_range(A.Uptr, p0, nv, wi.lane, eb, ee, cb0, ce0);
-            ww = warp_chain<T, true, true>(ww, eb, ee, cb0, ce0, A.Ucol, A.Uc, v.w, wi.lane);
-            if (ok) {
-                v.w[p] = ww;
-                acc.prod(ww, v.r[p]);
-            }
-        }
-        if (L == 0 && want_rho) {
-            double t[1] = {acc.value()};
-            block_reduce_store<1>(t, a.partials, SL_B, g.bid);
-        }
-        if (!group_sync(g)) return false;
-        pc.lap(CK_BWD + min(L, 63));
-    }
-    return true;
-}
-
-// One thread per row variants of the two sweeps.  The small last levels
-// (level >= tail_from, each at most one row per thread of a block) are run by
-// the group's first block alone with block-level barriers, followed by one
-// grid barrier, instead of one grid barrier per level.
+// ------------------------------------------------------ DIC sweeps ---------
+// Forward rows of one level: w = rD r - sum (rD a) w_lower, optionally with
+// the pending x/r update fused in (sum|r| into ares).
 template <class T>
 __device__ __forceinline__ void fwd_rows(const Mat<T>& A, Vecs<T> v, bool pending, T alpha, int r0, int r1, int first,
-                                         int stride, Acc<T>& acc)
+                                         int stride, Acc<T>& ares)
 {
-    constexpr int R = RowsPerThread<T>::R;
+    constexpr int R = ChainShape<T>::R, G = ChainShape<T>::G;
     for (int pb = r0 + first; pb < r1; pb += R * stride) {
         int p[R], e0[R], e1[R];
         T ww[R];
@@ -478,22 +360,24 @@ __device__ __forceinline__ void fwd_rows(const Mat<T>& A, Vecs<T> v, bool pendin
                 v.x[p[k]] = fmadd(alpha, v.p[p[k]], v.x[p[k]]);
                 rr = fmadd(-alpha, v.q[p[k]], rr);
                 v.r[p[k]] = rr;
-                acc.add(fabs(rr));
+                ares.add(fabs(rr));
             }
             ww[k] = ok ? mul_rn(A.rD[p[k]], rr) : T(0);
         }
-        rows_chain<T, R, false, true>(ww, e0, e1, A.Lcol, A.Lc, v.w);
+        rows_chain<T, R, G, false, true>(ww, e0, e1, A.Lcol, A.Lc, v.w);
 #pragma unroll
         for (int k = 0; k < R; k++)
             if (p[k] < r1) v.w[p[k]] = ww[k];
     }
 }
 
+// Backward rows of one level: w -= sum (rD a) w_upper (descending face
+// order); rho += w r.
 template <class T>
 __device__ __forceinline__ void bwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int r1, int first, int stride,
-                                         Acc<T>& acc)
+                                         Acc<T>& arho)
 {
-    constexpr int R = RowsPerThread<T>::R;
+    constexpr int R = ChainShape<T>::R, G = ChainShape<T>::G;
     for (int pb = r0 + first; pb < r1; pb += R * stride) {
         int p[R], e0[R], e1[R];
         T ww[R];
@@ -505,27 +389,31 @@ __device__ __forceinline__ void bwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int
             e1[k] = ok ? __ldg(A.Uptr + p[k] + 1) : 0;
             ww[k] = ok ? v.w[p[k]] : T(0);
         }
-        rows_chain<T, R, true, true>(ww, e0, e1, A.Ucol, A.Uc, v.w);
+        rows_chain<T, R, G, true, true>(ww, e0, e1, A.Ucol, A.Uc, v.w);
 #pragma unroll
         for (int k = 0; k < R; k++)
             if (p[k] < r1) {
                 v.w[p[k]] = ww[k];
-                acc.prod(ww[k], v.r[p[k]]);
+                arho.prod(ww[k], v.r[p[k]]);
             }
     }
 }
 
+// Forward sweep over all levels (the small last levels, level >= tail_from,
+// run on the group's first block alone with block-level barriers and one grid
+// barrier after them).  When `pending`, the x/r update is fused in and the
+// block partials of sum|r| go to slot A before the last grid barrier.
 template <class T>
-__device__ bool dic_forward_thread(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool pending, T alpha,
-                                   const Group& g, PhaseClock& pc)
+__device__ bool dic_forward(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool pending, T alpha, const Group& g,
+                            PhaseClock& pc)
 {
     RowIter it = rows_of(g);
-    Acc<T> acc;
+    Acc<T> ares;
     const int tail = min(a.tail_from, a.nlev);
     for (int L = 0; L < tail; L++) {
-        fwd_rows<T>(A, v, pending, alpha, a.lvl[L], a.lvl[L + 1], it.first, it.stride, acc);
+        fwd_rows<T>(A, v, pending, alpha, a.lvl[L], a.lvl[L + 1], it.first, it.stride, ares);
         if (L == a.nlev - 1 && pending) {
-            double t[1] = {acc.value()};
+            double t[1] = {ares.value()};
             block_reduce_store<1>(t, a.partials, SL_A, g.bid);
         }
         if (!group_sync(g)) return false;
@@ -534,12 +422,12 @@ __device__ bool dic_forward_thread(const SolveArgs& a, const Mat<T>& A, Vecs<T> 
     if (tail < a.nlev) {
         if (g.bid == 0) {
             for (int L = tail; L < a.nlev; L++) {
-                fwd_rows<T>(A, v, pending, alpha, a.lvl[L], a.lvl[L + 1], (int)threadIdx.x, (int)blockDim.x, acc);
+                fwd_rows<T>(A, v, pending, alpha, a.lvl[L], a.lvl[L + 1], (int)threadIdx.x, (int)blockDim.x, ares);
                 __syncthreads();
             }
         }
         if (pending) {
-            double t[1] = {acc.value()};
+            double t[1] = {ares.value()};
             block_reduce_store<1>(t, a.partials, SL_A, g.bid);
         }
         if (!group_sync(g)) return false;
@@ -548,31 +436,33 @@ __device__ bool dic_forward_thread(const SolveArgs& a, const Mat<T>& A, Vecs<T> 
     return true;
 }
 
+// Backward sweep (levels descending), with rho = w.r into slot B when
+// want_rho.
 template <class T>
-__device__ bool dic_backward_thread(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool want_rho, const Group& g,
-                                    PhaseClock& pc)
+__device__ bool dic_backward(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool want_rho, const Group& g,
+                             PhaseClock& pc)
 {
     RowIter it = rows_of(g);
-    Acc<T> acc;
+    Acc<T> arho;
     const int tail = min(a.tail_from, a.nlev);
     if (tail < a.nlev) {
         if (g.bid == 0) {
             for (int L = a.nlev - 1; L >= tail; L--) {
-                bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], (int)threadIdx.x, (int)blockDim.x, acc);
+                bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], (int)threadIdx.x, (int)blockDim.x, arho);
                 __syncthreads();
             }
         }
         if (tail == 0 && want_rho) {
-            double t[1] = {acc.value()};
+            double t[1] = {arho.value()};
             block_reduce_store<1>(t, a.partials, SL_B, g.bid);
         }
         if (!group_sync(g)) return false;
         pc.lap(CK_BWD + min(tail, 63));
     }
     for (int L = tail - 1; L >= 0; L--) {
-        bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], it.first, it.stride, acc);
+        bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], it.first, it.stride, arho);
         if (L == 0 && want_rho) {
-            double t[1] = {acc.value()};
+            double t[1] = {arho.value()};
             block_reduce_store<1>(t, a.partials, SL_B, g.bid);
         }
         if (!group_sync(g)) return false;
@@ -581,59 +471,7 @@ __device__ bool dic_backward_thread(const SolveArgs& a, const Mat<T>& A, Vecs<T>
     return true;
 }
 
-template <class T, int RM>
-__device__ __forceinline__ bool dic_forward(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool pending, T alpha,
-                                            const Group& g, PhaseClock& pc)
-{
-    if (RM) return dic_forward_warp<T>(a, A, v, pending, alpha, g, pc);
-    return dic_forward_thread<T>(a, A, v, pending, alpha, g, pc);
-}
-
-template <class T, int RM>
-__device__ __forceinline__ bool dic_backward(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool want_rho,
-                                             const Group& g, PhaseClock& pc)
-{
-    if (RM) return dic_backward_warp<T>(a, A, v, want_rho, g, pc);
-    return dic_backward_thread<T>(a, A, v, want_rho, g, pc);
-}
-
-// 16-byte vector of the working precision (float4 / double2): the streaming
-// passes move 16 bytes per load so that enough bytes are in flight per SM.
-template <class T>
-struct V16;
-template <>
-struct V16<float> {
-    using type = float4;
-    static constexpr int n = 4;
-};
-template <>
-struct V16<double> {
-    using type = double2;
-    static constexpr int n = 2;
-};
-// component-wise a*x + y and sum|x| on the vector types (register-only)
-__device__ __forceinline__ float4 vfma(float a, float4 x, float4 y)
-{
-    return make_float4(__fmaf_rn(a, x.x, y.x), __fmaf_rn(a, x.y, y.y), __fmaf_rn(a, x.z, y.z), __fmaf_rn(a, x.w, y.w));
-}
-__device__ __forceinline__ double2 vfma(double a, double2 x, double2 y)
-{
-    return make_double2(__fma_rn(a, x.x, y.x), __fma_rn(a, x.y, y.y));
-}
-template <class A>
-__device__ __forceinline__ void vadd_abs(A& acc, float4 r)
-{
-    acc.add(fabsf(r.x));
-    acc.add(fabsf(r.y));
-    acc.add(fabsf(r.z));
-    acc.add(fabsf(r.w));
-}
-template <class A>
-__device__ __forceinline__ void vadd_abs(A& acc, double2 r)
-{
-    acc.add(fabs(r.x));
-    acc.add(fabs(r.y));
-}
+// ----------------------------------------------------- streaming passes ---
 // Diagonal / no preconditioning in one pass, fused with the pending x/r
 // update; returns sum|r| (of the updated r) and rho = w.r through t[0], t[1].
 template <class T>
@@ -671,97 +509,33 @@ __device__ bool search_direction(const SolveArgs& a, Vecs<T> v, bool first, T be
     const int nv = a.n / W;
     VT* pv = reinterpret_cast<VT*>(v.p);
     const VT* wv = reinterpret_cast<const VT*>(v.w);
-    constexpr int R = 1;
-    for (int ib = it.first; ib < nv; ib += R * it.stride) {
-        VT pp[R], ww[R];
-#pragma unroll
-        for (int k = 0; k < R; k++) {
-            const int i = ib + k * it.stride;
-            if (i < nv) {
-                ww[k] = wv[i];
-                if (!first) pp[k] = pv[i];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < R; k++) {
-            const int i = ib + k * it.stride;
-            if (i < nv) {
-                pv[i] = first ? ww[k] : vfma(beta, pp[k], ww[k]);
-            }
-        }
+    for (int i = it.first; i < nv; i += it.stride) {
+        const VT ww = wv[i];
+        pv[i] = first ? ww : vfma(beta, pv[i], ww);
     }
     for (int p = nv * W + it.first; p < a.n; p += it.stride) v.p[p] = first ? v.w[p] : fmadd(beta, v.p[p], v.w[p]);
     return group_sync(g);
 }
 
 // q = A p and sigma = q.p
-template <class T, int RM>
+template <class T>
 __device__ bool amul_sigma(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const Group& g, double* sigma)
 {
+    constexpr int R = ChainShape<T>::R, G = ChainShape<T>::G;
     Acc<T> asig;
-    if (RM) {
-        const WarpIter wi = warps_of(g);
-        for (int p0 = 32 * wi.first; p0 < a.n; p0 += 32 * wi.stride) {
-            const int nv = min(32, a.n - p0), p = p0 + wi.lane;
-            const T qq = warp_amul_row<T>(A, v.p, p0, nv, wi.lane);
-            if (wi.lane < nv) {
-                v.q[p] = qq;
-                asig.prod(qq, v.p[p]);
+    RowIter it = rows_of(g);
+    for (int pb = it.first; pb < a.n; pb += R * it.stride) {
+        int p[R];
+        T y[R], pp[R];
+#pragma unroll
+        for (int k = 0; k < R; k++) p[k] = pb + k * it.stride;
+        amul_rows<T, R, G>(A, v.p, p, a.n, y, pp);
+#pragma unroll
+        for (int k = 0; k < R; k++)
+            if (p[k] < a.n) {
+                v.q[p[k]] = y[k];
+                asig.prod(y[k], pp[k]);
             }
-        }
-    } else {
-        RowIter it = rows_of(g);
-        constexpr int R = RowsPerThread<T>::R;
-        constexpr int G = R == 1 ? ChainGroup<T>::G : 4;
-        for (int pb = it.first; pb < a.n; pb += R * it.stride) {
-            int p[R], l0[R], nl[R], u0[R], nt[R];
-            T y[R], pp[R];
-#pragma unroll
-            for (int k = 0; k < R; k++) {
-                p[k] = pb + k * it.stride;
-                const bool ok = p[k] < a.n;
-                l0[k] = ok ? __ldg(A.Lptr + p[k]) : 0;
-                nl[k] = ok ? __ldg(A.Lptr + p[k] + 1) - l0[k] : 0;
-                u0[k] = ok ? __ldg(A.Uptr + p[k]) : 0;
-                nt[k] = ok ? nl[k] + __ldg(A.Uptr + p[k] + 1) - u0[k] : 0;
-                pp[k] = ok ? v.p[p[k]] : T(0);
-                y[k] = ok ? mul_rn(A.d[p[k]], pp[k]) : T(0);
-            }
-            for (int off = 0;; off += G) {
-                bool more = false;
-#pragma unroll
-                for (int k = 0; k < R; k++) more |= off < nt[k];
-                if (!more) break;
-                int c[R][G];
-                T cf[R][G], vv[R][G];
-#pragma unroll
-                for (int k = 0; k < R; k++)
-#pragma unroll
-                    for (int j = 0; j < G; j++) {
-                        const int kk = off + j;
-                        const bool low = kk < nl[k];
-                        const int e = low ? l0[k] + kk : u0[k] + (kk - nl[k]);
-                        const bool ok = kk < nt[k];
-                        c[k][j] = ok ? __ldg((low ? A.Lcol : A.Ucol) + e) : -1;
-                        cf[k][j] = ok ? (low ? A.La : A.Ua)[e] : T(0);
-                    }
-#pragma unroll
-                for (int k = 0; k < R; k++)
-#pragma unroll
-                    for (int j = 0; j < G; j++) vv[k][j] = c[k][j] >= 0 ? v.p[c[k][j]] : T(0);
-#pragma unroll
-                for (int k = 0; k < R; k++)
-#pragma unroll
-                    for (int j = 0; j < G; j++)
-                        if (c[k][j] >= 0) y[k] = fmadd(cf[k][j], vv[k][j], y[k]);
-            }
-#pragma unroll
-            for (int k = 0; k < R; k++)
-                if (p[k] < a.n) {
-                    v.q[p[k]] = y[k];
-                    asig.prod(y[k], pp[k]);
-                }
-        }
     }
     double sacc[1] = {asig.value()};
     block_reduce_store<1>(sacc, a.partials, SL_C, g.bid);
@@ -772,8 +546,8 @@ __device__ bool amul_sigma(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const
     return true;
 }
 
-// x += alpha p, r -= alpha q and sum|r| as a pass of its own (when the update
-// is not fused into the forward sweep); 16-byte loads, scalar tail.
+// x += alpha p, r -= alpha q and sum|r| as a pass of its own, ahead of the
+// forward sweep (16-byte loads, scalar tail).
 template <class T>
 __device__ bool update_pass(const SolveArgs& a, Vecs<T> v, T alpha, const Group& g, double* ressum)
 {
@@ -786,30 +560,11 @@ __device__ bool update_pass(const SolveArgs& a, Vecs<T> v, T alpha, const Group&
     VT* rv = reinterpret_cast<VT*>(v.r);
     const VT* pv = reinterpret_cast<const VT*>(v.p);
     const VT* qv = reinterpret_cast<const VT*>(v.q);
-    constexpr int R = 1;
-    for (int ib = it.first; ib < nv; ib += R * it.stride) {
-        VT xx[R], pp[R], qq[R], rr[R];
-#pragma unroll
-        for (int k = 0; k < R; k++) {
-            const int i = ib + k * it.stride;
-            if (i < nv) {
-                xx[k] = xv[i];
-                pp[k] = pv[i];
-                qq[k] = qv[i];
-                rr[k] = rv[i];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < R; k++) {
-            const int i = ib + k * it.stride;
-            if (i < nv) {
-                xx[k] = vfma(alpha, pp[k], xx[k]);
-                rr[k] = vfma(-alpha, qq[k], rr[k]);
-                vadd_abs(acc, rr[k]);
-                xv[i] = xx[k];
-                rv[i] = rr[k];
-            }
-        }
+    for (int i = it.first; i < nv; i += it.stride) {
+        const VT rr = vfma(-alpha, qv[i], rv[i]);
+        xv[i] = vfma(alpha, pv[i], xv[i]);
+        rv[i] = rr;
+        vadd_abs(acc, rr);
     }
     for (int p = nv * W + it.first; p < a.n; p += it.stride) {
         v.x[p] = fmadd(alpha, v.p[p], v.x[p]);
@@ -818,41 +573,42 @@ __device__ bool update_pass(const SolveArgs& a, Vecs<T> v, T alpha, const Group&
         acc.add(fabs(r1));
     }
     double t[1] = {acc.value()};
-    block_reduce_store<1>(t, a.partials, SL_A, g.bid);
+    block_reduce_store<1>(t, a.partials, SL_D, g.bid);
     if (!group_sync(g)) return false;
-    grid_reduce_read<1>(t, a.partials, SL_A, g.nblocks);
+    grid_reduce_read<1>(t, a.partials, SL_D, g.nblocks);
     *ressum = t[0];
     return true;
 }
 
-// w = M^-1 r (fused with the pending update); returns the updated sum|r| when
-// pending, and rho = w.r.  For DIC the residual norm is known after the
-// forward sweep; `after_fwd` runs there (it may replace r and ask for the
-// forward sweep to be redone) before the backward sweep computes rho.
-template <class T, int RM, class AfterFwd>
+// w = M^-1 r and rho = w.r, after the pending update (x += alpha p,
+// r -= alpha q, as its own pass or fused into the forward sweep), whose
+// sum|r| is handed to `after_update`: it stops the loop (1), lets it go on (0)
+// or replaces r and asks for w to be computed from the new r (2).
+// Returns 0 (w and rho ready), 2 (stop) or -1 (device error).
+template <class T, class AfterUpdate>
 __device__ int precondition(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool pending, T alpha, const Group& g,
-                            PhaseClock& pc, double* rho, AfterFwd after_fwd)
+                            PhaseClock& pc, double* rho, AfterUpdate after_update)
 {
-    double ressum = 0.0;
     if (a.precond == SPUMA_PRECOND_DIC) {
-        if (pending && !a.fuse_update) {
+        bool fused = pending && a.fuse_update;
+        if (pending && !fused) {
+            double ressum;
             if (!update_pass<T>(a, v, alpha, g, &ressum)) return -1;
-            pc.lap(CK_CORR);
-            const int act = after_fwd(ressum);
-            if (act == 1 || act < 0) return act;
-            if (!dic_forward<T, RM>(a, A, v, false, T(0), g, pc)) return -1;
-        } else {
-            if (!dic_forward<T, RM>(a, A, v, pending, alpha, g, pc)) return -1;
-            if (pending) {
-                double t[1];
-                grid_reduce_read<1>(t, a.partials, SL_A, g.nblocks);
-                ressum = t[0];
-            }
-            const int act = after_fwd(ressum);       // 0 continue, 1 stop, 2 redo (r replaced), -1 error
-            if (act == 1 || act < 0) return act;
-            if (act == 2 && !dic_forward<T, RM>(a, A, v, false, T(0), g, pc)) return -1;
+            pc.lap(CK_UPD);
+            const int act = after_update(ressum);
+            if (act < 0) return -1;
+            if (act == 1) return 2;
         }
-        if (!dic_backward<T, RM>(a, A, v, true, g, pc)) return -1;
+        if (!dic_forward<T>(a, A, v, fused, alpha, g, pc)) return -1;
+        if (fused) {
+            double t[1];
+            grid_reduce_read<1>(t, a.partials, SL_A, g.nblocks);
+            const int act = after_update(t[0]);
+            if (act < 0) return -1;
+            if (act == 1) return 2;
+            if (act == 2 && !dic_forward<T>(a, A, v, false, T(0), g, pc)) return -1;
+        }
+        if (!dic_backward<T>(a, A, v, true, g, pc)) return -1;
         double t[1];
         grid_reduce_read<1>(t, a.partials, SL_B, g.nblocks);
         *rho = t[0];
@@ -861,8 +617,9 @@ __device__ int precondition(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool
     double t[2];
     if (!diag_pass<T>(a, A, v, pending, alpha, g, t)) return -1;
     pc.lap(CK_DIAG);
-    const int act = after_fwd(t[0]);
-    if (act == 1 || act < 0) return act;
+    const int act = pending ? after_update(t[0]) : 0;
+    if (act < 0) return -1;
+    if (act == 1) return 2;
     if (act == 2 && !diag_pass<T>(a, A, v, false, T(0), g, t)) return -1;
     *rho = t[1];
     return 0;
@@ -870,7 +627,7 @@ __device__ int precondition(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool
 
 // PCG iterations on (A, v.r) from the current v.x (OpenFOAM recurrences).
 // Returns the iteration count, or -1 when a device error stopped the group.
-template <class T, int RM>
+template <class T>
 __device__ int pcg_loop(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, double nfac, double res0, double tol,
                         double rel_tol, int max_iter, int min_iter, double* res_out, int* singular,
                         const Group& g)
@@ -885,19 +642,18 @@ __device__ int pcg_loop(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, double n
     bool pending = false;
     for (;;) {
         rho_old = rho;
-        const int act = precondition<T, RM>(a, A, v, pending, alpha, g, pc, &rho, [&](double ressum) {
-            if (!pending) return 0;
+        const int st = precondition<T>(a, A, v, pending, alpha, g, pc, &rho, [&](double ressum) {
             res = ressum / nfac;
             n_it++;
             return ((n_it < max_iter && !converged(res, res0, tol, rel_tol)) || n_it < min_iter) ? 0 : 1;
         });
-        if (act < 0) return -1;
-        if (act == 1) break;
-        const bool first = n_it == 0;
+        if (st < 0) return -1;
+        if (st == 2) break;
+        const bool first = !pending;
         if (!search_direction<T>(a, v, first, first ? (T)0 : (T)(rho / rho_old), g)) return -1;
         pc.lap(CK_PUPD);
         double sigma;
-        if (!amul_sigma<T, RM>(a, A, v, g, &sigma)) return -1;
+        if (!amul_sigma<T>(a, A, v, g, &sigma)) return -1;
         pc.lap(CK_AMUL);
         pc.count(CK_ITERS);
         if (fabs(sigma) / nfac < 1e-300) {
@@ -912,9 +668,7 @@ __device__ int pcg_loop(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, double n
 }
 
 // FP64 refinement step of the mixed forms: x += xs (FP32 correction, reset to
-// 0), then r = b - A64 x with sum|r| (and max|r|), and r32 = float(r) (or
-// float(r / max|r|) for the restarted form, which scales).
-template <int RM>
+// 0) when fold, then r = b - A64 x with sum|r| and max|r|, and r32 = float(r).
 __device__ bool refine_residual(const SolveArgs& a, const Group& g, bool fold, double* ressum, double* rmax)
 {
     RowIter it = rows_of(g);
@@ -927,27 +681,12 @@ __device__ bool refine_residual(const SolveArgs& a, const Group& g, bool fold, d
         if (!group_sync(g)) return false;
     }
     double acc[1] = {0.0}, mx[1] = {0.0};
-    if (!RM) {
-        for (int p = it.first; p < a.n; p += it.stride) {
-            const double rr = a.b[p] - amul_row<double>(A64, a.x, p);
-            a.r[p] = rr;
-            a.ri[p] = (float)rr;
-            acc[0] += fabs(rr);
-            mx[0] = fmax(mx[0], fabs(rr));
-        }
-    } else {
-        const WarpIter wi = warps_of(g);
-        for (int p0 = 32 * wi.first; p0 < a.n; p0 += 32 * wi.stride) {
-            const int nv = min(32, a.n - p0), p = p0 + wi.lane;
-            const double ax = warp_amul_row<double>(A64, a.x, p0, nv, wi.lane);
-            if (wi.lane < nv) {
-                const double rr = a.b[p] - ax;
-                a.r[p] = rr;
-                a.ri[p] = (float)rr;
-                acc[0] += fabs(rr);
-                mx[0] = fmax(mx[0], fabs(rr));
-            }
-        }
+    for (int p = it.first; p < a.n; p += it.stride) {
+        const double rr = a.b[p] - amul_row<double>(A64, a.x, p);
+        a.r[p] = rr;
+        a.ri[p] = (float)rr;
+        acc[0] += fabs(rr);
+        mx[0] = fmax(mx[0], fabs(rr));
     }
     block_reduce_store<1>(acc, a.partials, SL_D, g.bid);
     block_max_store<1>(mx, a.partials, SL_D + 1, g.bid);
@@ -965,7 +704,6 @@ __device__ bool refine_residual(const SolveArgs& a, const Group& g, bool fold, d
 // FP32 residual has dropped by inner_rel_tol since the last replacement, the
 // FP32 residual claims convergence, or max_iter is reached; the search
 // direction is kept, so the Krylov space is never restarted.
-template <int RM>
 __device__ bool solve_mixed_reliable(const SolveArgs& a, const Group& g, double nfac, double res0,
                                      spuma_solver_perf& pf)
 {
@@ -986,13 +724,12 @@ __device__ bool solve_mixed_reliable(const SolveArgs& a, const Group& g, double 
         if (!group_sync(g)) return false;
         for (;;) {
             rho_old = rho;
-            const int act = precondition<float, RM>(a, A32, v, pending, alpha, g, pc, &rho, [&](double ressum) {
-                if (!pending) return 0;
+            const int st = precondition<float>(a, A32, v, pending, alpha, g, pc, &rho, [&](double ressum) {
                 n_it++;
                 const double ress = ressum / nfac;
                 if (!(ress < delta * rupd || converged(ress, res0, a.tol, a.rel_tol) || n_it >= a.max_iter)) return 0;
                 double rs, rm;
-                if (!refine_residual<RM>(a, g, true, &rs, &rm)) return -1;
+                if (!refine_residual(a, g, true, &rs, &rm)) return -1;
                 pc.lap(CK_RESID);
                 updates++;
                 res = rs / nfac;
@@ -1000,19 +737,19 @@ __device__ bool solve_mixed_reliable(const SolveArgs& a, const Group& g, double 
                 rupd = res;
                 return 2;
             });
-            if (act < 0) return false;
-            if (act == 1) break;
-            const bool first = n_it == 0;
+            if (st < 0) return false;
+            if (st == 2) break;
+            const bool first = !pending;
             if (!search_direction<float>(a, v, first, first ? 0.0f : (float)(rho / rho_old), g)) return false;
             pc.lap(CK_PUPD);
             double sigma;
-            if (!amul_sigma<float, RM>(a, A32, v, g, &sigma)) return false;
+            if (!amul_sigma<float>(a, A32, v, g, &sigma)) return false;
             pc.lap(CK_AMUL);
             pc.count(CK_ITERS);
             if (fabs(sigma) / nfac < 1e-300) {
                 singular = 1;
                 double rs, rm;
-                ok = refine_residual<RM>(a, g, true, &rs, &rm);
+                ok = refine_residual(a, g, true, &rs, &rm);
                 res = rs / nfac;
                 break;
             }
@@ -1083,7 +820,6 @@ __device__ void phase_store_x(const SolveArgs& a, const Group& g)
 
 // Mixed precision, restarted form: FP64 refinement around FP32 inner PCG
 // solves of A d = r / max|r| from d = 0 to inner_rel_tol.
-template <int RM>
 __device__ bool solve_mixed_restart(const SolveArgs& a, const Group& g, double nfac, spuma_solver_perf& pf)
 {
     RowIter it = rows_of(g);
@@ -1093,7 +829,7 @@ __device__ bool solve_mixed_restart(const SolveArgs& a, const Group& g, double n
     double res = 0.0, res0 = 0.0;
     for (;;) {
         double rs, rm;
-        if (!refine_residual<RM>(a, g, false, &rs, &rm)) return false;
+        if (!refine_residual(a, g, false, &rs, &rm)) return false;
         res = rs / nfac;
         if (outer == 0) res0 = res;
         if (res < a.tol || outer >= a.max_outer || singular) break;
@@ -1114,7 +850,7 @@ __device__ bool solve_mixed_restart(const SolveArgs& a, const Group& g, double n
         const double infac = ti[0] + 1e-20;
         const double ires0 = ti[0] / infac;
         double ires;
-        int n_in = pcg_loop<float, RM>(a, A32, vi, infac, ires0, 0.0, a.inner_rel_tol, a.max_iter, 1, &ires, &singular, g);
+        int n_in = pcg_loop<float>(a, A32, vi, infac, ires0, 0.0, a.inner_rel_tol, a.max_iter, 1, &ires, &singular, g);
         if (n_in < 0) return false;
         total += n_in;
         for (int p = it.first; p < a.n; p += it.stride) a.x[p] = fma(s, (double)vi.x[p], a.x[p]);
@@ -1130,7 +866,11 @@ __device__ bool solve_mixed_restart(const SolveArgs& a, const Group& g, double n
     return true;
 }
 
-template <int RM>
+// Kinds of persistent launch, one kernel each so that every kernel holds only
+// its own path (register allocation is per kernel).
+enum SolveKind { KIND_SETUP = 0, KIND_F64 = 1, KIND_MIXED = 2, KIND_MIXED_RESTART = 3 };
+
+template <int KIND>
 __device__ void run_system(const SolveArgs& a, const Group& g)
 {
     spuma_solver_perf pf;
@@ -1147,7 +887,7 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
         ok = phase_gather(a, g);
         if (ok) ok = phase_factor(a, g);
     }
-    if (ok && a.mode == MODE_PRECONDITION) {
+    if (KIND == KIND_SETUP && ok && a.mode == MODE_PRECONDITION) {
         // w = M^-1 r for r = b_orig, written to x_orig (FP64)
         RowIter it = rows_of(g);
         for (int p = it.first; p < a.n; p += it.stride) a.r[p] = a.b_orig[a.perm[p]];
@@ -1157,8 +897,8 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
         if (ok) {
             if (a.precond == SPUMA_PRECOND_DIC) {
                 PhaseClock pc(nullptr, g.bid);
-                ok = dic_forward<double, RM>(a, A, v, false, 0.0, g, pc);
-                if (ok) ok = dic_backward<double, RM>(a, A, v, false, g, pc);
+                ok = dic_forward<double>(a, A, v, false, 0.0, g, pc);
+                if (ok) ok = dic_backward<double>(a, A, v, false, g, pc);
             } else {
                 for (int p = it.first; p < a.n; p += it.stride)
                     a.w[p] = a.precond == SPUMA_PRECOND_DIAGONAL ? __dmul_rn(a.rD64[p], a.r[p]) : a.r[p];
@@ -1168,29 +908,31 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
         if (ok)
             for (int p = it.first; p < a.n; p += it.stride) a.x_orig[a.perm[p]] = a.w[p];
     }
-    if (ok && a.mode == MODE_SOLVE) {
-        double nfac = 1.0, res0 = 0.0;
-        ok = phase_init(a, g, &nfac, &res0);
-        if (ok) {
-            if (a.precision == SPUMA_MIXED) {
-                ok = solve_mixed_reliable<RM>(a, g, nfac, res0, pf);
-            } else if (a.precision == SPUMA_MIXED_RESTART) {
-                ok = solve_mixed_restart<RM>(a, g, nfac, pf);
-            } else {
-                Vecs<double> v{a.x, a.r, a.w, a.p, a.q};
-                double res;
-                int sing = 0;
-                int n_it = pcg_loop<double, RM>(a, mat_of<double>(a), v, nfac, res0, a.tol, a.rel_tol, a.max_iter,
-                                            a.min_iter, &res, &sing, g);
-                ok = n_it >= 0;
-                pf.initial_residual = res0;
-                pf.final_residual = res;
-                pf.n_iter = n_it < 0 ? 0 : n_it;
-                pf.converged = converged(res, res0, a.tol, a.rel_tol);
-                pf.singular = sing;
+    if constexpr (KIND != KIND_SETUP) {
+        if (ok && a.mode == MODE_SOLVE) {
+            double nfac = 1.0, res0 = 0.0;
+            ok = phase_init(a, g, &nfac, &res0);
+            if (ok) {
+                if constexpr (KIND == KIND_MIXED) {
+                    ok = solve_mixed_reliable(a, g, nfac, res0, pf);
+                } else if constexpr (KIND == KIND_MIXED_RESTART) {
+                    ok = solve_mixed_restart(a, g, nfac, pf);
+                } else {
+                    Vecs<double> v{a.x, a.r, a.w, a.p, a.q};
+                    double res;
+                    int sing = 0;
+                    int n_it = pcg_loop<double>(a, mat_of<double>(a), v, nfac, res0, a.tol, a.rel_tol, a.max_iter,
+                                                a.min_iter, &res, &sing, g);
+                    ok = n_it >= 0;
+                    pf.initial_residual = res0;
+                    pf.final_residual = res;
+                    pf.n_iter = n_it < 0 ? 0 : n_it;
+                    pf.converged = converged(res, res0, a.tol, a.rel_tol);
+                    pf.singular = sing;
+                }
             }
+            if (ok && !a.no_store) phase_store_x(a, g);
         }
-        if (ok && !a.no_store) phase_store_x(a, g);
     }
     if (g.bid == 0 && threadIdx.x == 0 && a.perf) {
         __threadfence();
@@ -1200,14 +942,15 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
     }
 }
 
-template <int RM>
-__global__ void __launch_bounds__(RM ? 256 : 1024, RM ? 3 : 1) k_solve(SolveArgs a, unsigned long long timeout_ns)
+template <int KIND>
+__global__ void __launch_bounds__(1024, 1) k_solve(SolveArgs a, unsigned long long timeout_ns)
 {
     Group g{reinterpret_cast<unsigned*>(a.status + DS_BARRIER), a.status, (int)gridDim.x, (int)blockIdx.x, timeout_ns};
-    run_system<RM>(a, g);
+    run_system<KIND>(a, g);
 }
 
-__global__ void __launch_bounds__(256, 3) k_solve_batch(BatchTable t, unsigned long long timeout_ns)
+template <int KIND>
+__global__ void __launch_bounds__(256, 2) k_solve_batch(BatchTable t, unsigned long long timeout_ns)
 {
     __shared__ SolveArgs sa;
     int s = 0;
@@ -1216,26 +959,25 @@ __global__ void __launch_bounds__(256, 3) k_solve_batch(BatchTable t, unsigned l
     __syncthreads();
     Group g{reinterpret_cast<unsigned*>(sa.status + DS_BARRIER), sa.status, t.split[s + 1] - t.split[s],
             (int)blockIdx.x - t.split[s], timeout_ns};
-    run_system<0>(sa, g);
+    run_system<KIND>(sa, g);
 }
 
-// Stand-alone Amul on the prepared matrix (internal order).
-template <class T>
-__global__ void __launch_bounds__(256) k_amul_prepared_thread(int n, Mat<T> A, const T* __restrict__ x,
-                                                              T* __restrict__ y)
-{
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) y[p] = amul_row<T>(A, x, p);
-}
-
+// Stand-alone Amul on the prepared matrix (internal order): the PCG's Amul
+// phase as a kernel of its own.
 template <class T>
 __global__ void __launch_bounds__(256) k_amul_prepared(int n, Mat<T> A, const T* __restrict__ x, T* __restrict__ y)
 {
-    const int lane = threadIdx.x & 31;
-    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    for (int p0 = 32 * w0; p0 < n; p0 += 32 * nw) {
-        const int nv = min(32, n - p0);
-        const T yy = warp_amul_row<T>(A, x, p0, nv, lane);
-        if (lane < nv) y[p0 + lane] = yy;
+    constexpr int R = ChainShape<T>::R, G = ChainShape<T>::G;
+    const int stride = gridDim.x * blockDim.x;
+    for (int pb = blockIdx.x * blockDim.x + threadIdx.x; pb < n; pb += R * stride) {
+        int p[R];
+        T yy[R], xp[R];
+#pragma unroll
+        for (int k = 0; k < R; k++) p[k] = pb + k * stride;
+        amul_rows<T, R, G>(A, x, p, n, yy, xp);
+#pragma unroll
+        for (int k = 0; k < R; k++)
+            if (p[k] < n) y[p[k]] = yy[k];
     }
 }
 
@@ -1300,17 +1042,6 @@ SolveArgs make_args(spuma_ldu_t h)
     return a;
 }
 
-// Row-processing variant of the persistent solver (SPUMA_ROW_MODE=1 selects
-// the warp-cooperative chunks; default one thread per row).
-static int row_mode()
-{
-    static int m = [] {
-        const char* e = getenv("SPUMA_ROW_MODE");
-        return e && atoi(e) == 1 ? 1 : 0;
-    }();
-    return m;
-}
-
 static int fuse_update_default()
 {
     static int m = [] {
@@ -1320,19 +1051,45 @@ static int fuse_update_default()
     return m;
 }
 
+static int kind_of(const SolveArgs& a)
+{
+    if (a.mode != MODE_SOLVE) return KIND_SETUP;
+    if (a.precision == SPUMA_MIXED) return KIND_MIXED;
+    if (a.precision == SPUMA_MIXED_RESTART) return KIND_MIXED_RESTART;
+    return KIND_F64;
+}
+
+static const void* solve_kernel(int kind)
+{
+    switch (kind) {
+    case KIND_SETUP: return (const void*)k_solve<KIND_SETUP>;
+    case KIND_MIXED: return (const void*)k_solve<KIND_MIXED>;
+    case KIND_MIXED_RESTART: return (const void*)k_solve<KIND_MIXED_RESTART>;
+    default: return (const void*)k_solve<KIND_F64>;
+    }
+}
+
+static const void* batch_kernel(int kind)
+{
+    switch (kind) {
+    case KIND_MIXED: return (const void*)k_solve_batch<KIND_MIXED>;
+    case KIND_MIXED_RESTART: return (const void*)k_solve_batch<KIND_MIXED_RESTART>;
+    default: return (const void*)k_solve_batch<KIND_F64>;
+    }
+}
+
 static std::mutex g_occ_mu;
 static std::map<int, int> g_occ;   // (kernel, block threads) -> co-resident blocks per SM
 
-int solve_blocks_per_sm(int threads, bool batch)
+int solve_blocks_per_sm(int threads, bool batch, int kind)
 {
     std::lock_guard<std::mutex> lk(g_occ_mu);
-    const int key = threads * 4 + (batch ? 2 : 0) + row_mode();
+    const int key = (threads * 2 + (batch ? 1 : 0)) * 4 + kind;
     auto it = g_occ.find(key);
     if (it != g_occ.end()) return it->second;
     int nb = 0;
-    cudaError_t e = batch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve_batch, threads, 0)
-                          : (row_mode() ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<1>, threads, 0)
-                                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_solve<0>, threads, 0));
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch ? batch_kernel(kind) : solve_kernel(kind),
+                                                                  threads, 0);
     if (e != cudaSuccess) nb = 0;
     g_occ[key] = nb;
     return nb;
@@ -1341,7 +1098,7 @@ int solve_blocks_per_sm(int threads, bool batch)
 int default_threads(const spuma_solver_controls* ctl)
 {
     if (ctl && ctl->block_threads > 0) return ctl->block_threads;
-    return row_mode() ? 256 : 1024;
+    return 1024;
 }
 
 // First level of the run of small last levels (each with at most `threads`
@@ -1359,12 +1116,11 @@ int tail_level(spuma_ldu_t h, int threads)
 
 spuma_status launch_solve(spuma_ldu_t h, const SolveArgs& a, int threads, cudaStream_t s)
 {
-    const int tmax = row_mode() ? 256 : 1024;
-    if (threads < 32 || threads > tmax || threads % 32) {
-        set_error("block_threads must be a multiple of 32 in [32, 256] (1024 for the thread-per-row kernel)");
+    if (threads < 32 || threads > 1024 || threads % 32) {
+        set_error("block_threads must be a multiple of 32 in [32, 1024]");
         return SPUMA_ERR_INVALID_ARG;
     }
-    int per_sm = solve_blocks_per_sm(threads, false);
+    int per_sm = solve_blocks_per_sm(threads, false, kind_of(a));
     if (per_sm < 1) { set_error("solver kernel cannot be resident"); return SPUMA_ERR_CUDA; }
     // SPUMA_SOLVE_BLOCKS_PER_SM caps the co-resident blocks per SM used by the
     // persistent solver (a tuning override; default: all that fit)
@@ -1378,7 +1134,6 @@ spuma_status launch_solve(spuma_ldu_t h, const SolveArgs& a, int threads, cudaSt
     SPUMA_CUDA(cudaMemsetAsync(h->at<char>(h->L.bar), 0, h->L.status + 256 - h->L.bar, s));
     unsigned long long tns = barrier_timeout_ns();
     SolveArgs b = a;
-    b.row_mode = row_mode();
     b.tail_from = tail_level(h, threads);
     // SPUMA_FUSE_UPDATE=1 fuses the x/r update into the forward DIC sweep
     // (default: a pass of its own ahead of the sweep)
@@ -1388,13 +1143,12 @@ spuma_status launch_solve(spuma_ldu_t h, const SolveArgs& a, int threads, cudaSt
         SPUMA_CUDA(cudaMemsetAsync(b.phase_clk, 0, 8 * 256, s));
     }
     void* args[] = {(void*)&b, (void*)&tns};
-    const void* fn = b.row_mode ? (const void*)k_solve<1> : (const void*)k_solve<0>;
-    SPUMA_CUDA(cudaLaunchCooperativeKernel(fn, grid, threads, args, 0, s));
+    SPUMA_CUDA(cudaLaunchCooperativeKernel(solve_kernel(kind_of(b)), grid, threads, args, 0, s));
     count_launch();
     return SPUMA_OK;
 }
 
-spuma_status launch_batch_kernel(const BatchTable& t, int grid, int threads, cudaStream_t s)
+spuma_status launch_batch_kernel(const BatchTable& t, int grid, int threads, int kind, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -1406,8 +1160,17 @@ spuma_status launch_batch_kernel(const BatchTable& t, int grid, int threads, cud
     cfg.attrs = at;
     cfg.numAttrs = 1;
     unsigned long long tns = barrier_timeout_ns();
-    SPUMA_CUDA(cudaLaunchKernelEx(&cfg, k_solve_batch, t, tns));
+    BatchTable tt = t;
+    void* args[] = {(void*)&tt, (void*)&tns};
+    SPUMA_CUDA(cudaLaunchKernelExC(&cfg, batch_kernel(kind), args));
     return SPUMA_OK;
+}
+
+int batch_kind(int precision)
+{
+    if (precision == SPUMA_MIXED) return KIND_MIXED;
+    if (precision == SPUMA_MIXED_RESTART) return KIND_MIXED_RESTART;
+    return KIND_F64;
 }
 
 void fill_controls(SolveArgs& a, const spuma_solver_controls* ctl)
@@ -1511,16 +1274,10 @@ spuma_status spuma_amul_prepared(spuma_ldu_t h, int32_t precision, const void* x
     cudaStream_t s = (cudaStream_t)stream;
     if (precision == SPUMA_F64) {
         Mat<double> A{a.Lptr, a.Lcol, a.La64, a.Lc64, a.Uptr, a.Ucol, a.Ua64, a.Uc64, a.d64, a.rD64};
-        if (row_mode())
-            k_amul_prepared<double><<<g, 256, 0, s>>>(h->n, A, (const double*)x, (double*)y);
-        else
-            k_amul_prepared_thread<double><<<g, 256, 0, s>>>(h->n, A, (const double*)x, (double*)y);
+        k_amul_prepared<double><<<g, 256, 0, s>>>(h->n, A, (const double*)x, (double*)y);
     } else {
         Mat<float> A{a.Lptr, a.Lcol, a.La32, a.Lc32, a.Uptr, a.Ucol, a.Ua32, a.Uc32, a.d32, a.rD32};
-        if (row_mode())
-            k_amul_prepared<float><<<g, 256, 0, s>>>(h->n, A, (const float*)x, (float*)y);
-        else
-            k_amul_prepared_thread<float><<<g, 256, 0, s>>>(h->n, A, (const float*)x, (float*)y);
+        k_amul_prepared<float><<<g, 256, 0, s>>>(h->n, A, (const float*)x, (float*)y);
     }
     count_launch();
     SPUMA_CUDA(cudaGetLastError());
