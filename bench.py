@@ -29,7 +29,7 @@ METRIC = "PCG time to 1e-8 rel. residual @8M cells (FP64 vs mixed); Amul HBM GB/
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # Iteration counts of this seeded workload (mixed: inner iterations, outer
 # steps), used only to project the CPU oracle's bounded sample to a full solve.
-PROJECTION_ITERS = {"inner": 1000, "outer": 3}
+PROJECTION_ITERS = {"inner": 795, "outer": 5}
 
 
 def parse():
@@ -39,8 +39,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=200, help="mesh side (default 200: 8.0M cells)")
-    ap.add_argument("--cpu-iters", type=int, default=8, help="oracle inner iterations in the CPU sample")
+    ap.add_argument("--cpu-iters", type=int, default=24, help="oracle inner iterations in the CPU sample")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch", action="store_true",
+                    help="time the batched workload instead: 64 systems, cells log-uniform in 1e4..5e5")
     return ap.parse_args()
 
 
@@ -152,9 +154,10 @@ def cpu_sample(case, n_inner_sample: int):
     oracle.amul(m.lower, m.upper_addr, dg, up, case.b)
     t_res = time.perf_counter() - t0
     proj = t_asm + fixed + max(0, PROJECTION_ITERS["outer"] - 1) * t_res + PROJECTION_ITERS["inner"] * per_inner
-    sample = (f"oracle assembly + DIC factor + 2 FP64 residuals + {2 + n_inner_sample} FP32 inner iterations "
-              f"(two timed runs, per-iteration cost by difference), projected to "
-              f"{PROJECTION_ITERS['inner']} inner iterations and {PROJECTION_ITERS['outer']} outer steps")
+    sample = (f"oracle (restarted mixed form, one refinement step): assembly + DIC factor + 2 FP64 residuals + "
+              f"{2 + n_inner_sample} FP32 iterations (two timed runs, per-iteration cost by difference), "
+              f"projected to {PROJECTION_ITERS['inner']} FP32 iterations and {PROJECTION_ITERS['outer']} FP64 "
+              f"residuals (the GPU's counts for this workload)")
     return proj * 1e3, dict(sample=sample, per_inner_ms=per_inner * 1e3, assembly_ms=t_asm * 1e3,
                             cpu_seconds=t_asm + t_a + t_b + t_res)
 
@@ -191,11 +194,72 @@ def config_of(case, args):
             "l2": "inputs larger than L2 (workspace and per-iteration streams > 129 MB)"}
 
 
+def run_batch(args, rank, world, local):
+    """64 independent systems (jittered, permuted hex blocks, side lengths from
+    cell counts log-uniform in 1e4..5e5, seed 5) in one persistent launch
+    replayed from a CUDA graph, FP64 and mixed, autotuned block size/split."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    import hexmesh
+    __graft_entry__.build()
+    from paper_2512_22215_gb300 import MIXED, BatchSolve, LduMesh, SolverControls
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sides = hexmesh.batch_sizes(64, seed=5)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    Ms, D, U, B, X = [], [], [], [], []
+    for k, n in enumerate(sides):
+        c = hexmesh.pressure_case(n, jitter=0.2, permute=True, seed=500 + k, lognormal_gamma=True)
+        m = c.mesh
+        M = LduMesh(m.lower, m.upper_addr, m.n_cells, device=dev, centres=m.c)
+        up, dg = M.assemble_laplacian(T(m.sf), T(m.c), T(c.gamma), T(m.bface_cell), T(m.bface_sf), T(m.bface_cf),
+                                      T(c.bgamma), T(c.btype))
+        Ms.append(M)
+        D.append(dg)
+        U.append(up)
+        B.append(T(c.b))
+        X.append(torch.zeros(m.n_cells, dtype=torch.float64, device=dev))
+    cells = sum(M.n_cells for M in Ms)
+    out = {}
+    for name, ctl in [("fp64", SolverControls(precond=2, tolerance=1e-8)),
+                      ("mixed", SolverControls(precond=2, precision=MIXED, tolerance=1e-8))]:
+        bs = BatchSolve(Ms, D, U, B, X, ctl, autotune=True)
+        for x in X:
+            x.zero_()
+        bs.run()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            for x in X:
+                x.zero_()
+            a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            bs.run()
+            c.record()
+            c.synchronize()
+            ts.append(a.elapsed_time(c))
+        res = bs.results()
+        ts.sort()
+        out[name] = {"ms": round(ts[len(ts) // 2], 3), "max_iters": max(r["n_iter"] for r in res),
+                     "all_converged": all(r["converged"] == 1 for r in res),
+                     "block_threads": bs.block_threads, "grid_blocks": bs.grid_blocks}
+    line = {"metric": "batched PCG time to 1e-8, 64 systems", "value": out["mixed"]["ms"], "unit": "ms",
+            "higher_is_better": False, "n_gpus": world, "steps": args.steps, "data": "synthetic",
+            "config": {"workload": "64 jittered permuted hex blocks, cells log-uniform in 1e4..5e5, seed 5",
+                       "cells": cells}, "fp64": out["fp64"], "mixed": out["mixed"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.batch:
+        run_batch(args, rank, world, local)
         return
     import numpy as np
     import torch
@@ -219,7 +283,7 @@ def main():
     gamma, b = T(case.gamma), T(case.b)
     x = torch.zeros(N, dtype=torch.float64, device=dev)
     perf = perf_tensor(1, dev)
-    ctl_mixed = SolverControls(precond=2, precision=MIXED, tolerance=1e-8, inner_rel_tol=1e-4, max_outer=30)
+    ctl_mixed = SolverControls(precond=2, precision=MIXED, tolerance=1e-8, inner_rel_tol=1e-2)
     ctl_f64 = SolverControls(precond=2, tolerance=1e-8)
     s = torch.cuda.current_stream()
 
@@ -288,17 +352,19 @@ def main():
     yi = torch.empty_like(xi)
     xi32, yi32 = xi.float(), torch.empty(N, dtype=torch.float32, device=dev)
 
-    def time_amul(xv, yv, reps=20):
+    def time_amul(xv, yv, reps=50):
+        """Back-to-back launches between two events: the GPU never waits for
+        the host between them, so the average is the kernel's own time."""
         for _ in range(3):
             M.amul_prepared(xv, yv)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
-        for a_, c_ in ev:
-            a_.record(s)
-            M.amul_prepared(xv, yv)
-            c_.record(s)
         torch.cuda.synchronize()
-        ts = sorted(a_.elapsed_time(c_) for a_, c_ in ev)
-        return ts[len(ts) // 2] * 1e3   # us
+        a_, c_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(s)
+        for _ in range(reps):
+            M.amul_prepared(xv, yv)
+        c_.record(s)
+        c_.synchronize()
+        return a_.elapsed_time(c_) / reps * 1e3   # us
 
     amul64_us = time_amul(xi, yi)
     amul32_us = time_amul(xi32, yi32)
