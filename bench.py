@@ -27,6 +27,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PCG time to 1e-8 rel. residual @8M cells (FP64 vs mixed); Amul HBM GB/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the mixed-precision solve kernel on this workload, from the one-pass ncu
+# capture summarised in profiles/k_solve_mixed_200cubed_dram.md; valid only
+# for the solver source it was taken with (checked by hash, else null).
+TRAFFIC = {"solve_cu_sha1": "e35fd896a356cdc68d0d410f162b1baae1d642e6",
+           "bytes_per_launch": 1048346599680 + 147395920384}
 # Iteration counts of this seeded workload (mixed: inner iterations, outer
 # steps), used only to project the CPU oracle's bounded sample to a full solve.
 PROJECTION_ITERS = {"inner": 795, "outer": 5}
@@ -71,6 +77,18 @@ def load_peaks():
             d = json.load(fh)
         return d, "measured"
     return PEAKS_FALLBACK, "fallback"
+
+
+def traffic_bytes(n: int):
+    """The recorded DRAM traffic per launch, when the solver source still
+    matches the capture and the workload is the captured one; else None."""
+    import hashlib
+    if n != 200:
+        return None
+    src = os.path.join(ROOT, "paper_2512_22215_gb300", "csrc", "solve.cu")
+    with open(src, "rb") as fh:
+        sha = hashlib.sha1(fh.read()).hexdigest()
+    return TRAFFIC["bytes_per_launch"] if sha == TRAFFIC["solve_cu_sha1"] else None
 
 
 def workload_bytes(n_cells: int, n_faces: int):
@@ -406,7 +424,7 @@ def main():
     f64_bytes = p_f64["n_iter"] * wb["it64"]
     roofline = {"kernel": "k_solve (persistent mixed-precision solve, one launch per solve)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "peak_kind": peak_kind, "traffic": None,
+                "peak_kind": peak_kind, "traffic": traffic_bytes(args.n),
                 "algorithmic_bytes": int(mixed_bytes),
                 "basis": "inner iterations x (76N + 36F) + (outer + 1) FP64 residuals x (16F + 40N)"}
 

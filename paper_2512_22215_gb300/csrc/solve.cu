@@ -45,13 +45,20 @@ __device__ __forceinline__ Mat<float> mat_of<float>(const SolveArgs& a)
     return Mat<float>{a.Lptr, a.Lcol, a.La32, a.Lc32, a.Uptr, a.Ucol, a.Ua32, a.Uc32, a.d32, a.rD32};
 }
 
-// Group sizes of the row chains: a row's entries are taken in groups whose
-// column and coefficient loads are issued together, then the gathers, then
-// the FMAs in entry order (two memory round trips per group, not per entry).
-// FP64 rows run one per thread with groups of 6 (a hex-mesh row has at most
-// 6 entries); FP32 rows run two per thread in lockstep with groups of 4.
+// Shapes of the row chains: a row's entries are taken in groups whose column
+// and coefficient loads are issued together, then the gathers, then the FMAs
+// in entry order (two memory round trips per group, not per entry).  FP64 rows
+// run one per thread, FP32 rows two per thread in lockstep.  Groups of 6 in
+// the DIC sweeps (a hex-mesh row has at most 6 entries on either side); the
+// Amul takes a row's lower and upper entries as one list, in groups of 6
+// (FP64) or 4 (FP32).  Chosen by measurement on the 200^3 workload.
 template <class T>
 struct ChainShape {
+    static constexpr int R = sizeof(T) == 4 ? 2 : 1;
+    static constexpr int G = 6;
+};
+template <class T>
+struct AmulShape {
     static constexpr int R = sizeof(T) == 4 ? 2 : 1;
     static constexpr int G = sizeof(T) == 4 ? 4 : 6;
 };
@@ -142,7 +149,7 @@ __device__ __forceinline__ T amul_row(const Mat<T>& A, const T* x, int p)
 {
     int pp[1] = {p};
     T y[1], xp[1];
-    amul_rows<T, 1, ChainShape<T>::G>(A, x, pp, p + 1, y, xp);
+    amul_rows<T, 1, AmulShape<T>::G>(A, x, pp, p + 1, y, xp);
     return y[0];
 }
 
@@ -399,18 +406,16 @@ __device__ __forceinline__ void bwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int
     }
 }
 
-// Forward sweep over all levels (the small last levels, level >= tail_from,
-// run on the group's first block alone with block-level barriers and one grid
-// barrier after them).  When `pending`, the x/r update is fused in and the
-// block partials of sum|r| go to slot A before the last grid barrier.
+// Forward sweep over all levels, one grid barrier per level.  When `pending`,
+// the x/r update is fused in and the block partials of sum|r| go to slot A
+// before the last grid barrier.  (Used by the fused-update form.)
 template <class T>
 __device__ bool dic_forward(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool pending, T alpha, const Group& g,
                             PhaseClock& pc)
 {
     RowIter it = rows_of(g);
     Acc<T> ares;
-    const int tail = min(a.tail_from, a.nlev);
-    for (int L = 0; L < tail; L++) {
+    for (int L = 0; L < a.nlev; L++) {
         fwd_rows<T>(A, v, pending, alpha, a.lvl[L], a.lvl[L + 1], it.first, it.stride, ares);
         if (L == a.nlev - 1 && pending) {
             double t[1] = {ares.value()};
@@ -419,49 +424,19 @@ __device__ bool dic_forward(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool
         if (!group_sync(g)) return false;
         pc.lap(CK_FWD + min(L, 63));
     }
-    if (tail < a.nlev) {
-        if (g.bid == 0) {
-            for (int L = tail; L < a.nlev; L++) {
-                fwd_rows<T>(A, v, pending, alpha, a.lvl[L], a.lvl[L + 1], (int)threadIdx.x, (int)blockDim.x, ares);
-                __syncthreads();
-            }
-        }
-        if (pending) {
-            double t[1] = {ares.value()};
-            block_reduce_store<1>(t, a.partials, SL_A, g.bid);
-        }
-        if (!group_sync(g)) return false;
-        pc.lap(CK_FWD + min(tail, 63));
-    }
     return true;
 }
 
-// Backward sweep (levels descending), with rho = w.r into slot B when
-// want_rho.
+// Backward sweep (levels descending, one grid barrier per level), with
+// rho = w.r into slot B.
 template <class T>
-__device__ bool dic_backward(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool want_rho, const Group& g,
-                             PhaseClock& pc)
+__device__ bool dic_backward(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const Group& g, PhaseClock& pc)
 {
     RowIter it = rows_of(g);
     Acc<T> arho;
-    const int tail = min(a.tail_from, a.nlev);
-    if (tail < a.nlev) {
-        if (g.bid == 0) {
-            for (int L = a.nlev - 1; L >= tail; L--) {
-                bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], (int)threadIdx.x, (int)blockDim.x, arho);
-                __syncthreads();
-            }
-        }
-        if (tail == 0 && want_rho) {
-            double t[1] = {arho.value()};
-            block_reduce_store<1>(t, a.partials, SL_B, g.bid);
-        }
-        if (!group_sync(g)) return false;
-        pc.lap(CK_BWD + min(tail, 63));
-    }
-    for (int L = tail - 1; L >= 0; L--) {
+    for (int L = a.nlev - 1; L >= 0; L--) {
         bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], it.first, it.stride, arho);
-        if (L == 0 && want_rho) {
+        if (L == 0) {
             double t[1] = {arho.value()};
             block_reduce_store<1>(t, a.partials, SL_B, g.bid);
         }
@@ -521,7 +496,7 @@ __device__ bool search_direction(const SolveArgs& a, Vecs<T> v, bool first, T be
 template <class T>
 __device__ bool amul_sigma(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const Group& g, double* sigma)
 {
-    constexpr int R = ChainShape<T>::R, G = ChainShape<T>::G;
+    constexpr int R = AmulShape<T>::R, G = AmulShape<T>::G;
     Acc<T> asig;
     RowIter it = rows_of(g);
     for (int pb = it.first; pb < a.n; pb += R * it.stride) {
@@ -590,25 +565,27 @@ __device__ int precondition(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool
                             PhaseClock& pc, double* rho, AfterUpdate after_update)
 {
     if (a.precond == SPUMA_PRECOND_DIC) {
-        bool fused = pending && a.fuse_update;
-        if (pending && !fused) {
-            double ressum;
-            if (!update_pass<T>(a, v, alpha, g, &ressum)) return -1;
-            pc.lap(CK_UPD);
-            const int act = after_update(ressum);
-            if (act < 0) return -1;
-            if (act == 1) return 2;
-        }
-        if (!dic_forward<T>(a, A, v, fused, alpha, g, pc)) return -1;
-        if (fused) {
+        if (a.fuse_update && pending) {
+            if (!dic_forward<T>(a, A, v, true, alpha, g, pc)) return -1;
             double t[1];
             grid_reduce_read<1>(t, a.partials, SL_A, g.nblocks);
             const int act = after_update(t[0]);
             if (act < 0) return -1;
             if (act == 1) return 2;
             if (act == 2 && !dic_forward<T>(a, A, v, false, T(0), g, pc)) return -1;
+            if (!dic_backward<T>(a, A, v, g, pc)) return -1;
+        } else {
+            if (pending) {
+                double ressum;
+                if (!update_pass<T>(a, v, alpha, g, &ressum)) return -1;
+                pc.lap(CK_UPD);
+                const int act = after_update(ressum);
+                if (act < 0) return -1;
+                if (act == 1) return 2;
+            }
+            if (!dic_forward<T>(a, A, v, false, T(0), g, pc)) return -1;
+            if (!dic_backward<T>(a, A, v, g, pc)) return -1;
         }
-        if (!dic_backward<T>(a, A, v, true, g, pc)) return -1;
         double t[1];
         grid_reduce_read<1>(t, a.partials, SL_B, g.nblocks);
         *rho = t[0];
@@ -898,7 +875,7 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
             if (a.precond == SPUMA_PRECOND_DIC) {
                 PhaseClock pc(nullptr, g.bid);
                 ok = dic_forward<double>(a, A, v, false, 0.0, g, pc);
-                if (ok) ok = dic_backward<double>(a, A, v, false, g, pc);
+                if (ok) ok = dic_backward<double>(a, A, v, g, pc);
             } else {
                 for (int p = it.first; p < a.n; p += it.stride)
                     a.w[p] = a.precond == SPUMA_PRECOND_DIAGONAL ? __dmul_rn(a.rD64[p], a.r[p]) : a.r[p];
@@ -967,7 +944,7 @@ __global__ void __launch_bounds__(256, 2) k_solve_batch(BatchTable t, unsigned l
 template <class T>
 __global__ void __launch_bounds__(256) k_amul_prepared(int n, Mat<T> A, const T* __restrict__ x, T* __restrict__ y)
 {
-    constexpr int R = ChainShape<T>::R, G = ChainShape<T>::G;
+    constexpr int R = AmulShape<T>::R, G = AmulShape<T>::G;
     const int stride = gridDim.x * blockDim.x;
     for (int pb = blockIdx.x * blockDim.x + threadIdx.x; pb < n; pb += R * stride) {
         int p[R];
@@ -1004,7 +981,7 @@ SolveArgs make_args(spuma_ldu_t h)
     a.n = h->n;
     a.nf = h->nf;
     a.nlev = h->nlev;
-    a.tail_from = h->nlev;
+
     a.lvl = h->at<int>(L.lvl);
     a.perm = h->at<int>(L.perm);
     a.Lptr = h->at<int>(L.Lptr);
@@ -1101,19 +1078,6 @@ int default_threads(const spuma_solver_controls* ctl)
     return 1024;
 }
 
-// First level of the run of small last levels (each with at most `threads`
-// rows) that the solver's first block handles alone; SPUMA_TAIL_ROWS
-// overrides the row limit (0 disables).
-int tail_level(spuma_ldu_t h, int threads)
-{
-    int limit = threads;
-    if (const char* e = getenv("SPUMA_TAIL_ROWS")) limit = atoi(e);
-    int t = h->nlev;
-    while (t > 1 && (int64_t)h->h_lvl[t] - h->h_lvl[t - 1] <= limit) t--;
-    // keep at least two levels in the tail, else the single grid barrier saves nothing
-    return (h->nlev - t >= 2) ? t : h->nlev;
-}
-
 spuma_status launch_solve(spuma_ldu_t h, const SolveArgs& a, int threads, cudaStream_t s)
 {
     if (threads < 32 || threads > 1024 || threads % 32) {
@@ -1134,7 +1098,6 @@ spuma_status launch_solve(spuma_ldu_t h, const SolveArgs& a, int threads, cudaSt
     SPUMA_CUDA(cudaMemsetAsync(h->at<char>(h->L.bar), 0, h->L.status + 256 - h->L.bar, s));
     unsigned long long tns = barrier_timeout_ns();
     SolveArgs b = a;
-    b.tail_from = tail_level(h, threads);
     // SPUMA_FUSE_UPDATE=1 fuses the x/r update into the forward DIC sweep
     // (default: a pass of its own ahead of the sweep)
     b.fuse_update = fuse_update_default();

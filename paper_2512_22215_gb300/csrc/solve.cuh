@@ -14,7 +14,6 @@ struct SolveArgs {
     int precision;         // spuma_precision (F64 or MIXED)
     int zero_x0;           // start from x = 0 instead of reading x_orig
     int no_store;          // leave x_orig untouched (autotuner trial runs)
-    int tail_from;         // levels >= tail_from are small enough for the group's first block alone
     int fuse_update;       // 1: x/r update fused into the forward DIC sweep, 0: its own pass
     int max_iter, min_iter, max_outer;
     double tol, rel_tol, inner_rel_tol;
