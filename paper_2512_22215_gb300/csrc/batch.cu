@@ -226,6 +226,7 @@ spuma_status spuma_batch_create(int32_t n_sys, const spuma_ldu_t* hs, const doub
         a.b_orig = b[k];
         a.x_orig = x[k];
         a.perf = perf + k;
+        a.tail_from = hs[k]->nlev;        // batch groups run every level on all their blocks
         hs[k]->prepared_precond = ctl->precond;
     }
     // trial runs of the tuner start from 0 and leave the caller's x alone

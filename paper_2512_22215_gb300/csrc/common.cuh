@@ -12,6 +12,7 @@
 namespace spuma {
 
 constexpr int kMaxBlocks = 4096;       // partial-sum slots per reduction
+constexpr int kEllMax = 8;             // widest row of the fixed-width Amul layout
 constexpr int kSlots = 8;              // reduction slots
 constexpr int kMaxBatch = 1024;        // systems per batched launch
 constexpr int kWarp = 32;
@@ -82,7 +83,11 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 // multiple of the group size.  No generation read before arriving, no status
 // reload after: an error sets the word's top bit, which ends every wait.
 // Every wait is bounded by a time limit: when it expires the block records
-// SPUMA_ERR_DEVICE_TIMEOUT and the caller unwinds.
+// SPUMA_ERR_DEVICE_TIMEOUT and the caller unwinds.  Ordering needs no extra
+// fence: the arrival is a gpu-scope acquire-release add made after the
+// block's threads met (release is cumulative over the writes they made
+// before), and the wait ends on a gpu-scope acquire load of the word that the
+// last arrival's add wrote; the block's threads meet again after it.
 struct Group {
     unsigned* word;        // arrival word (status + DS_BARRIER)
     int* status;           // device status words
@@ -97,7 +102,6 @@ __device__ __forceinline__ bool group_sync(const Group& g)
     __shared__ int s_err;
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
         const unsigned old = atom_add_acq_rel(g.word, 1u);
         bool err = (old & kErrBit) != 0;
         if (!err) {
@@ -120,7 +124,6 @@ __device__ __forceinline__ bool group_sync(const Group& g)
                 }
             }
         }
-        __threadfence();
         s_err = err ? 1 : 0;
     }
     __syncthreads();
@@ -228,6 +231,13 @@ struct Mat {
     const T* Uc;
     const T* d;        // diagonal
     const T* rD;       // DIC / diagonal reciprocal
+    // the Amul's entries of each row (lower ascending, then upper ascending)
+    // in a column-major fixed-width layout: entry j of row p at j * ell_stride
+    // + p (column -1: padding); ell_w = 0 when the mesh does not use it
+    const int* Ecol;
+    const T* Ea;
+    int ell_w;
+    int ell_stride;
 };
 
 // Workspace layout: one carve function used for sizing and for create.
@@ -239,6 +249,8 @@ struct Layout {
     // matrix
     size_t La64, Ua64, Lc64, Uc64, d64, rD64;
     size_t La32, Ua32, Lc32, Uc32, d32, rD32;
+    // fixed-width Amul layout: ell_slots entries
+    size_t ell_slots, Ecol, Ea64, Ea32;
     // vectors
     size_t x64, r64, w64, p64, q64, b64;
     size_t x32, r32, w32, p32, q32;
@@ -259,6 +271,7 @@ struct spuma_ldu {
     size_t ws_bytes = 0;
     spuma::Layout L;
     int prepared_precond = -1;
+    int ell_w = 0;                     // width of the fixed-width Amul layout (0: not used)
     std::vector<int32_t> h_lvl;
     template <class T>
     T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }

@@ -37,21 +37,23 @@ __device__ __forceinline__ Mat<T> mat_of(const SolveArgs& a);
 template <>
 __device__ __forceinline__ Mat<double> mat_of<double>(const SolveArgs& a)
 {
-    return Mat<double>{a.Lptr, a.Lcol, a.La64, a.Lc64, a.Uptr, a.Ucol, a.Ua64, a.Uc64, a.d64, a.rD64};
+    return Mat<double>{a.Lptr, a.Lcol, a.La64, a.Lc64, a.Uptr, a.Ucol, a.Ua64, a.Uc64, a.d64, a.rD64,
+                       a.Ecol, a.Ea64, a.ell_w, a.n};
 }
 template <>
 __device__ __forceinline__ Mat<float> mat_of<float>(const SolveArgs& a)
 {
-    return Mat<float>{a.Lptr, a.Lcol, a.La32, a.Lc32, a.Uptr, a.Ucol, a.Ua32, a.Uc32, a.d32, a.rD32};
+    return Mat<float>{a.Lptr, a.Lcol, a.La32, a.Lc32, a.Uptr, a.Ucol, a.Ua32, a.Uc32, a.d32, a.rD32,
+                      a.Ecol, a.Ea32, a.ell_w, a.n};
 }
 
 // Shapes of the row chains: a row's entries are taken in groups whose column
 // and coefficient loads are issued together, then the gathers, then the FMAs
 // in entry order (two memory round trips per group, not per entry).  FP64 rows
 // run one per thread, FP32 rows two per thread in lockstep.  Groups of 6 in
-// the DIC sweeps (a hex-mesh row has at most 6 entries on either side); the
-// Amul takes a row's lower and upper entries as one list, in groups of 6
-// (FP64) or 4 (FP32).  Chosen by measurement on the 200^3 workload.
+// the DIC sweeps (a hex-mesh row has at most 6 entries on either side) and in
+// the Amul, which takes a row's lower and upper entries as one list (a whole
+// hex-mesh row in one group).  Chosen by measurement on the 200^3 workload.
 template <class T>
 struct ChainShape {
     static constexpr int R = sizeof(T) == 4 ? 2 : 1;
@@ -60,7 +62,7 @@ struct ChainShape {
 template <class T>
 struct AmulShape {
     static constexpr int R = sizeof(T) == 4 ? 2 : 1;
-    static constexpr int G = sizeof(T) == 4 ? 4 : 6;
+    static constexpr int G = 6;
 };
 
 // R rows' chains in lockstep; each row takes its entries [e0, e1) in its own
@@ -103,6 +105,38 @@ template <class T, int R, int G>
 __device__ __forceinline__ void amul_rows(const Mat<T>& A, const T* x, const int (&p)[R], int n, T (&y)[R],
                                           T (&xp)[R])
 {
+    if (A.ell_w > 0) {
+        // fixed-width layout: no row extents to load, entries coalesced
+#pragma unroll
+        for (int k = 0; k < R; k++) {
+            const bool ok = p[k] < n;
+            xp[k] = ok ? x[p[k]] : T(0);
+            y[k] = ok ? mul_rn(A.d[p[k]], xp[k]) : T(0);
+        }
+        for (int j0 = 0; j0 < A.ell_w; j0 += G) {
+            int c[R][G];
+            T cf[R][G], vv[R][G];
+#pragma unroll
+            for (int k = 0; k < R; k++)
+#pragma unroll
+                for (int j = 0; j < G; j++) {
+                    const bool ok = p[k] < n && j0 + j < A.ell_w;
+                    const size_t e = (size_t)(j0 + j) * A.ell_stride + p[k];
+                    c[k][j] = ok ? __ldg(A.Ecol + e) : -1;
+                    cf[k][j] = ok ? A.Ea[e] : T(0);
+                }
+#pragma unroll
+            for (int k = 0; k < R; k++)
+#pragma unroll
+                for (int j = 0; j < G; j++) vv[k][j] = c[k][j] >= 0 ? x[c[k][j]] : T(0);
+#pragma unroll
+            for (int k = 0; k < R; k++)
+#pragma unroll
+                for (int j = 0; j < G; j++)
+                    if (c[k][j] >= 0) y[k] = fmadd(cf[k][j], vv[k][j], y[k]);
+        }
+        return;
+    }
     int l0[R], nl[R], u0[R], nt[R];
 #pragma unroll
     for (int k = 0; k < R; k++) {
@@ -292,6 +326,15 @@ __device__ bool phase_gather(const SolveArgs& a, const Group& g)
         a.d64[p] = dv;
         a.d32[p] = (float)dv;
         bad |= !isfinite(dv);
+        if (a.ell_w > 0) {
+            const int l0 = a.Lptr[p], nl = a.Lptr[p + 1] - l0, u0 = a.Uptr[p], nt = nl + a.Uptr[p + 1] - u0;
+            for (int j = 0; j < a.ell_w; j++) {
+                const double v = j < nl ? a.upper_orig[a.Lface[l0 + j]]
+                                        : (j < nt ? a.upper_orig[a.Uface[u0 + j - nl]] : 0.0);
+                a.Ea64[(size_t)j * a.n + p] = v;
+                a.Ea32[(size_t)j * a.n + p] = (float)v;
+            }
+        }
     }
     if (bad) flag_error(a.status, SPUMA_ERR_NONFINITE, -1);
     return group_sync(g);
@@ -346,35 +389,33 @@ __device__ bool phase_factor(const SolveArgs& a, const Group& g)
 }
 
 // ------------------------------------------------------ DIC sweeps ---------
-// Forward rows of one level: w = rD r - sum (rD a) w_lower, optionally with
-// the pending x/r update fused in (sum|r| into ares).
+// Forward rows of one level: w = rD r - sum (rD a) w_lower (ascending face
+// order); with `rho` (top level: no upper neighbours, so w is final here)
+// also rho += w r.
 template <class T>
-__device__ __forceinline__ void fwd_rows(const Mat<T>& A, Vecs<T> v, bool pending, T alpha, int r0, int r1, int first,
-                                         int stride, Acc<T>& ares)
+__device__ __forceinline__ void fwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int r1, int first, int stride, bool rho,
+                                         Acc<T>& arho)
 {
     constexpr int R = ChainShape<T>::R, G = ChainShape<T>::G;
     for (int pb = r0 + first; pb < r1; pb += R * stride) {
         int p[R], e0[R], e1[R];
-        T ww[R];
+        T ww[R], rr[R];
 #pragma unroll
         for (int k = 0; k < R; k++) {
             p[k] = pb + k * stride;
             const bool ok = p[k] < r1;
             e0[k] = ok ? __ldg(A.Lptr + p[k]) : 0;
             e1[k] = ok ? __ldg(A.Lptr + p[k] + 1) : 0;
-            T rr = ok ? v.r[p[k]] : T(0);
-            if (pending && ok) {
-                v.x[p[k]] = fmadd(alpha, v.p[p[k]], v.x[p[k]]);
-                rr = fmadd(-alpha, v.q[p[k]], rr);
-                v.r[p[k]] = rr;
-                ares.add(fabs(rr));
-            }
-            ww[k] = ok ? mul_rn(A.rD[p[k]], rr) : T(0);
+            rr[k] = ok ? v.r[p[k]] : T(0);
+            ww[k] = ok ? mul_rn(A.rD[p[k]], rr[k]) : T(0);
         }
         rows_chain<T, R, G, false, true>(ww, e0, e1, A.Lcol, A.Lc, v.w);
 #pragma unroll
         for (int k = 0; k < R; k++)
-            if (p[k] < r1) v.w[p[k]] = ww[k];
+            if (p[k] < r1) {
+                v.w[p[k]] = ww[k];
+                if (rho) arho.prod(ww[k], rr[k]);
+            }
     }
 }
 
@@ -406,41 +447,50 @@ __device__ __forceinline__ void bwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int
     }
 }
 
-// Forward sweep over all levels, one grid barrier per level.  When `pending`,
-// the x/r update is fused in and the block partials of sum|r| go to slot A
-// before the last grid barrier.  (Used by the fused-update form.)
+// w = M^-1 r with the DIC factor, and the block partials of rho = w.r in
+// slot B before the last grid barrier.  Forward sweep over levels 0 ..
+// nlev-1, backward over nlev-2 .. 0 (the top level has no upper neighbours:
+// its backward step would leave w as it is, so its rho terms are taken in the
+// forward step), one grid barrier per level.  The small last levels
+// (level >= tail_from) run on the group's first block alone, forward then
+// backward, with block-level barriers and one grid barrier after them.
 template <class T>
-__device__ bool dic_forward(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool pending, T alpha, const Group& g,
-                            PhaseClock& pc)
+__device__ bool dic_apply(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const Group& g, PhaseClock& pc)
 {
-    RowIter it = rows_of(g);
-    Acc<T> ares;
-    for (int L = 0; L < a.nlev; L++) {
-        fwd_rows<T>(A, v, pending, alpha, a.lvl[L], a.lvl[L + 1], it.first, it.stride, ares);
-        if (L == a.nlev - 1 && pending) {
-            double t[1] = {ares.value()};
-            block_reduce_store<1>(t, a.partials, SL_A, g.bid);
-        }
-        if (!group_sync(g)) return false;
-        pc.lap(CK_FWD + min(L, 63));
-    }
-    return true;
-}
-
-// Backward sweep (levels descending, one grid barrier per level), with
-// rho = w.r into slot B.
-template <class T>
-__device__ bool dic_backward(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const Group& g, PhaseClock& pc)
-{
-    RowIter it = rows_of(g);
+    const RowIter it = rows_of(g);
+    const int nlev = a.nlev, tail = min(a.tail_from, nlev);
+    const int tid = (int)threadIdx.x, bs = (int)blockDim.x;
     Acc<T> arho;
-    for (int L = a.nlev - 1; L >= 0; L--) {
-        bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], it.first, it.stride, arho);
-        if (L == 0) {
+    auto end_step = [&](bool last) {
+        if (last) {
             double t[1] = {arho.value()};
             block_reduce_store<1>(t, a.partials, SL_B, g.bid);
         }
-        if (!group_sync(g)) return false;
+        return group_sync(g);
+    };
+    if (nlev == 0) return end_step(true);
+    for (int L = 0; L < tail; L++) {
+        fwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], it.first, it.stride, L == nlev - 1, arho);
+        if (!end_step(nlev == 1)) return false;
+        pc.lap(CK_FWD + min(L, 63));
+    }
+    if (tail < nlev) {
+        if (g.bid == 0) {
+            for (int L = tail; L < nlev; L++) {
+                fwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], tid, bs, L == nlev - 1, arho);
+                __syncthreads();
+            }
+            for (int L = nlev - 2; L >= tail; L--) {
+                bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], tid, bs, arho);
+                __syncthreads();
+            }
+        }
+        if (!end_step(tail == 0)) return false;
+        pc.lap(CK_FWD + min(tail, 63));
+    }
+    for (int L = min(tail, nlev - 1) - 1; L >= 0; L--) {
+        bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], it.first, it.stride, arho);
+        if (!end_step(L == 0)) return false;
         pc.lap(CK_BWD + min(L, 63));
     }
     return true;
@@ -556,36 +606,25 @@ __device__ bool update_pass(const SolveArgs& a, Vecs<T> v, T alpha, const Group&
 }
 
 // w = M^-1 r and rho = w.r, after the pending update (x += alpha p,
-// r -= alpha q, as its own pass or fused into the forward sweep), whose
-// sum|r| is handed to `after_update`: it stops the loop (1), lets it go on (0)
-// or replaces r and asks for w to be computed from the new r (2).
+// r -= alpha q, a pass of its own for DIC, fused into the diagonal pass
+// otherwise), whose sum|r| is handed to `after_update`: it stops the loop
+// (1), lets it go on (0) or replaces r and asks for w to be computed from the
+// new r (2).
 // Returns 0 (w and rho ready), 2 (stop) or -1 (device error).
 template <class T, class AfterUpdate>
 __device__ int precondition(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool pending, T alpha, const Group& g,
                             PhaseClock& pc, double* rho, AfterUpdate after_update)
 {
     if (a.precond == SPUMA_PRECOND_DIC) {
-        if (a.fuse_update && pending) {
-            if (!dic_forward<T>(a, A, v, true, alpha, g, pc)) return -1;
-            double t[1];
-            grid_reduce_read<1>(t, a.partials, SL_A, g.nblocks);
-            const int act = after_update(t[0]);
+        if (pending) {
+            double ressum;
+            if (!update_pass<T>(a, v, alpha, g, &ressum)) return -1;
+            pc.lap(CK_UPD);
+            const int act = after_update(ressum);
             if (act < 0) return -1;
             if (act == 1) return 2;
-            if (act == 2 && !dic_forward<T>(a, A, v, false, T(0), g, pc)) return -1;
-            if (!dic_backward<T>(a, A, v, g, pc)) return -1;
-        } else {
-            if (pending) {
-                double ressum;
-                if (!update_pass<T>(a, v, alpha, g, &ressum)) return -1;
-                pc.lap(CK_UPD);
-                const int act = after_update(ressum);
-                if (act < 0) return -1;
-                if (act == 1) return 2;
-            }
-            if (!dic_forward<T>(a, A, v, false, T(0), g, pc)) return -1;
-            if (!dic_backward<T>(a, A, v, g, pc)) return -1;
         }
+        if (!dic_apply<T>(a, A, v, g, pc)) return -1;
         double t[1];
         grid_reduce_read<1>(t, a.partials, SL_B, g.nblocks);
         *rho = t[0];
@@ -874,8 +913,7 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
         if (ok) {
             if (a.precond == SPUMA_PRECOND_DIC) {
                 PhaseClock pc(nullptr, g.bid);
-                ok = dic_forward<double>(a, A, v, false, 0.0, g, pc);
-                if (ok) ok = dic_backward<double>(a, A, v, g, pc);
+                ok = dic_apply<double>(a, A, v, g, pc);
             } else {
                 for (int p = it.first; p < a.n; p += it.stride)
                     a.w[p] = a.precond == SPUMA_PRECOND_DIAGONAL ? __dmul_rn(a.rD64[p], a.r[p]) : a.r[p];
@@ -981,6 +1019,7 @@ SolveArgs make_args(spuma_ldu_t h)
     a.n = h->n;
     a.nf = h->nf;
     a.nlev = h->nlev;
+    a.tail_from = h->nlev;
 
     a.lvl = h->at<int>(L.lvl);
     a.perm = h->at<int>(L.perm);
@@ -996,6 +1035,10 @@ SolveArgs make_args(spuma_ldu_t h)
     a.Uc64 = h->at<double>(L.Uc64);
     a.d64 = h->at<double>(L.d64);
     a.rD64 = h->at<double>(L.rD64);
+    a.Ecol = h->at<int>(L.Ecol);
+    a.Ea64 = h->at<double>(L.Ea64);
+    a.Ea32 = h->at<float>(L.Ea32);
+    a.ell_w = h->ell_w;
     a.La32 = h->at<float>(L.La32);
     a.Ua32 = h->at<float>(L.Ua32);
     a.Lc32 = h->at<float>(L.Lc32);
@@ -1017,15 +1060,6 @@ SolveArgs make_args(spuma_ldu_t h)
     a.bar = h->at<unsigned>(L.bar);
     a.status = h->at<int>(L.status);
     return a;
-}
-
-static int fuse_update_default()
-{
-    static int m = [] {
-        const char* e = getenv("SPUMA_FUSE_UPDATE");
-        return e && atoi(e) == 1 ? 1 : 0;
-    }();
-    return m;
 }
 
 static int kind_of(const SolveArgs& a)
@@ -1078,29 +1112,48 @@ int default_threads(const spuma_solver_controls* ctl)
     return 1024;
 }
 
+// Blocks of the persistent single-system solver: one per row chunk of
+// `threads` rows, at most all co-resident blocks (SPUMA_SOLVE_BLOCKS_PER_SM
+// caps the blocks per SM, a tuning override).  0 when the kernel cannot be
+// resident.
+int solve_grid(spuma_ldu_t h, int threads, int kind)
+{
+    int per_sm = solve_blocks_per_sm(threads, false, kind);
+    if (per_sm < 1) return 0;
+    if (const char* env = getenv("SPUMA_SOLVE_BLOCKS_PER_SM")) {
+        int v = atoi(env);
+        if (v >= 1 && v < per_sm) per_sm = v;
+    }
+    int64_t want = ((int64_t)h->n + threads - 1) / threads;
+    int64_t maxg = std::min<int64_t>((int64_t)per_sm * h->num_sms, kMaxBlocks);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, maxg));
+}
+
+// First level of the run of small last levels (each with at most `threads`
+// rows) that the solver's first block handles alone; SPUMA_TAIL_ROWS
+// overrides the row limit (0 disables).
+int tail_level(spuma_ldu_t h, int threads)
+{
+    int limit = threads;
+    if (const char* e = getenv("SPUMA_TAIL_ROWS")) limit = atoi(e);
+    int t = h->nlev;
+    while (t > 1 && (int64_t)h->h_lvl[t] - h->h_lvl[t - 1] <= limit) t--;
+    // keep at least two levels in the tail, else the single grid barrier saves nothing
+    return (h->nlev - t >= 2) ? t : h->nlev;
+}
+
 spuma_status launch_solve(spuma_ldu_t h, const SolveArgs& a, int threads, cudaStream_t s)
 {
     if (threads < 32 || threads > 1024 || threads % 32) {
         set_error("block_threads must be a multiple of 32 in [32, 1024]");
         return SPUMA_ERR_INVALID_ARG;
     }
-    int per_sm = solve_blocks_per_sm(threads, false, kind_of(a));
-    if (per_sm < 1) { set_error("solver kernel cannot be resident"); return SPUMA_ERR_CUDA; }
-    // SPUMA_SOLVE_BLOCKS_PER_SM caps the co-resident blocks per SM used by the
-    // persistent solver (a tuning override; default: all that fit)
-    if (const char* env = getenv("SPUMA_SOLVE_BLOCKS_PER_SM")) {
-        int v = atoi(env);
-        if (v >= 1 && v < per_sm) per_sm = v;
-    }
-    int64_t want = ((int64_t)a.n + threads - 1) / threads;
-    int64_t maxg = std::min<int64_t>((int64_t)per_sm * h->num_sms, kMaxBlocks);
-    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, maxg));
+    const int grid = solve_grid(h, threads, kind_of(a));
+    if (grid < 1) { set_error("solver kernel cannot be resident"); return SPUMA_ERR_CUDA; }
     SPUMA_CUDA(cudaMemsetAsync(h->at<char>(h->L.bar), 0, h->L.status + 256 - h->L.bar, s));
     unsigned long long tns = barrier_timeout_ns();
     SolveArgs b = a;
-    // SPUMA_FUSE_UPDATE=1 fuses the x/r update into the forward DIC sweep
-    // (default: a pass of its own ahead of the sweep)
-    b.fuse_update = fuse_update_default();
+    b.tail_from = tail_level(h, threads);
     if (getenv("SPUMA_PHASE_CLOCKS")) {
         b.phase_clk = h->at<long long>(h->L.clk);
         SPUMA_CUDA(cudaMemsetAsync(b.phase_clk, 0, 8 * 256, s));
@@ -1236,10 +1289,12 @@ spuma_status spuma_amul_prepared(spuma_ldu_t h, int32_t precision, const void* x
     int g = std::min((h->n + 255) / 256, h->num_sms * 16);
     cudaStream_t s = (cudaStream_t)stream;
     if (precision == SPUMA_F64) {
-        Mat<double> A{a.Lptr, a.Lcol, a.La64, a.Lc64, a.Uptr, a.Ucol, a.Ua64, a.Uc64, a.d64, a.rD64};
+        Mat<double> A{a.Lptr, a.Lcol, a.La64, a.Lc64, a.Uptr, a.Ucol, a.Ua64, a.Uc64, a.d64, a.rD64,
+                      a.Ecol, a.Ea64, a.ell_w, a.n};
         k_amul_prepared<double><<<g, 256, 0, s>>>(h->n, A, (const double*)x, (double*)y);
     } else {
-        Mat<float> A{a.Lptr, a.Lcol, a.La32, a.Lc32, a.Uptr, a.Ucol, a.Ua32, a.Uc32, a.d32, a.rD32};
+        Mat<float> A{a.Lptr, a.Lcol, a.La32, a.Lc32, a.Uptr, a.Ucol, a.Ua32, a.Uc32, a.d32, a.rD32,
+                     a.Ecol, a.Ea32, a.ell_w, a.n};
         k_amul_prepared<float><<<g, 256, 0, s>>>(h->n, A, (const float*)x, (float*)y);
     }
     count_launch();

@@ -14,7 +14,7 @@ struct SolveArgs {
     int precision;         // spuma_precision (F64 or MIXED)
     int zero_x0;           // start from x = 0 instead of reading x_orig
     int no_store;          // leave x_orig untouched (autotuner trial runs)
-    int fuse_update;       // 1: x/r update fused into the forward DIC sweep, 0: its own pass
+    int tail_from;         // levels >= tail_from are small enough for the group's first block alone
     int max_iter, min_iter, max_outer;
     double tol, rel_tol, inner_rel_tol;
     const int* lvl;        // [nlev+1] level starts (internal order)
@@ -28,6 +28,10 @@ struct SolveArgs {
     const int *Lptr, *Lcol, *Lface, *Uptr, *Ucol, *Uface;
     double *La64, *Ua64, *Lc64, *Uc64, *d64, *rD64;
     float *La32, *Ua32, *Lc32, *Uc32, *d32, *rD32;
+    const int* Ecol;       // fixed-width Amul layout (ell_w > 0): columns, entry j of row p at j n + p
+    double* Ea64;
+    float* Ea32;
+    int ell_w;
     // internal vectors
     double *x, *r, *w, *p, *q, *b;
     float *xi, *ri, *wi, *pi, *qi;

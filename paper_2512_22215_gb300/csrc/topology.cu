@@ -67,6 +67,12 @@ Layout make_layout(int64_t n, int64_t nf)
     L.Uc32 = take(f4f);
     L.d32 = take(f4n);
     L.rD32 = take(f4n);
+    // fixed-width Amul layout: used when the widest row times n fits 2F + n
+    // slots (no more than one padding slot per row on average)
+    L.ell_slots = 2 * (size_t)nf + (size_t)n;
+    L.Ecol = take(4 * L.ell_slots);
+    L.Ea64 = take(8 * L.ell_slots);
+    L.Ea32 = take(4 * L.ell_slots);
     L.x64 = take(d8n);
     L.r64 = take(d8n);
     L.w64 = take(d8n);
@@ -431,6 +437,38 @@ __global__ void k_internal_fill(int n, const int* __restrict__ perm, const int* 
     }
 }
 
+// Widest row of the Amul (lower + upper entries) into *w (atomic max).
+__global__ void k_row_width(int n, const int* __restrict__ Lptr, const int* __restrict__ Uptr, int* w)
+{
+    int m = 0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+        m = max(m, Lptr[p + 1] - Lptr[p] + Uptr[p + 1] - Uptr[p]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(w, m);
+}
+
+// Whether the fixed-width Amul layout is used for a widest row of w entries.
+__host__ __device__ inline bool ell_fits(int w, int64_t n, size_t slots)
+{
+    return w >= 1 && w <= kEllMax && (size_t)w * (size_t)n <= slots;
+}
+
+// Columns of the fixed-width Amul layout: entry j of row p (its lower
+// entries in ascending face order, then its upper ones) at j n + p, -1 past
+// the row's end.  Does nothing unless the layout fits.
+__global__ void k_ell_fill(int n, size_t slots, const int* __restrict__ wptr, const int* __restrict__ Lptr,
+                           const int* __restrict__ Lcol, const int* __restrict__ Uptr, const int* __restrict__ Ucol,
+                           int* Ecol)
+{
+    const int w = *wptr;
+    if (!ell_fits(w, n, slots)) return;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const int l0 = Lptr[p], nl = Lptr[p + 1] - l0, u0 = Uptr[p], nt = nl + Uptr[p + 1] - u0;
+        for (int j = 0; j < w; j++)
+            Ecol[(size_t)j * n + p] = j < nl ? Lcol[l0 + j] : (j < nt ? Ucol[u0 + j - nl] : -1);
+    }
+}
+
 spuma_status scan_exclusive_ext(const int* in, int64_t n, int* out, int* tmp, cudaStream_t s)
 {
     return scan_exclusive(in, n, out, tmp, s);
@@ -649,6 +687,14 @@ spuma_status spuma_ldu_create_with_centres(int32_t n, int32_t nf, const int32_t*
             n, h->at<int>(L.perm), h->at<int>(L.iperm), lo_start, lo_face, lo_col, own_start, uaddr, Lptr, Uptr,
             h->at<int>(L.Lcol), h->at<int>(L.Lface), h->at<int>(L.Ucol), h->at<int>(L.Uface));
         count_launch();
+        // fixed-width Amul layout (the widest row decides; read back below)
+        int* wdev = h->at<int>(L.args);
+        CU(cudaMemsetAsync(wdev, 0, sizeof(int), s));
+        k_row_width<<<grid_for(n, T, h->num_sms), T, 0, s>>>(n, Lptr, Uptr, wdev);
+        k_ell_fill<<<grid_for(n, T, h->num_sms), T, 0, s>>>(n, L.ell_slots, wdev, Lptr, h->at<int>(L.Lcol), Uptr,
+                                                            h->at<int>(L.Ucol), h->at<int>(L.Ecol));
+        count_launch(2);
+        CU(cudaMemcpyAsync(&h->ell_w, wdev, sizeof(int), cudaMemcpyDeviceToHost, s));
         h->h_lvl.resize(nlev + 1);
         CU(cudaMemcpyAsync(h->h_lvl.data(), lvl, 4 * (size_t)(nlev + 1), cudaMemcpyDeviceToHost, s));
     }
@@ -659,6 +705,7 @@ spuma_status spuma_ldu_create_with_centres(int32_t n, int32_t nf, const int32_t*
 #undef CHK
 #undef CU
     h->nlev = nlev;
+    if (!ell_fits(h->ell_w, n, L.ell_slots)) h->ell_w = 0;
     *out = h;
     return SPUMA_OK;
 }
