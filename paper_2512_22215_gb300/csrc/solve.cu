@@ -59,6 +59,18 @@ struct ChainShape {
     static constexpr int R = sizeof(T) == 4 ? 2 : 1;
     static constexpr int G = 6;
 };
+// Software-pipelined fixed-width Amul: R rows per round, whole rows of up to
+// G entries.  Where it is used was decided by measurement at 200^3: inside
+// the persistent solver for FP64 (219 -> 200 us per Amul; FP32 keeps its two
+// rows per thread in lockstep, 112 against 131 us pipelined), and in the
+// stand-alone prepared Amul for FP32 (107 -> 101 us; FP64 168 against 176 us).
+template <class T>
+struct PipeShape {
+    static constexpr int R = 1;
+    static constexpr int G = 6;
+    static constexpr bool in_solver = sizeof(T) == 8;
+    static constexpr bool stand_alone = sizeof(T) == 4;
+};
 template <class T>
 struct AmulShape {
     static constexpr int R = sizeof(T) == 4 ? 2 : 1;
@@ -175,6 +187,73 @@ __device__ __forceinline__ void amul_rows(const Mat<T>& A, const T* x, const int
 #pragma unroll
             for (int j = 0; j < G; j++)
                 if (c[k][j] >= 0) y[k] = fmadd(cf[k][j], vv[k][j], y[k]);
+    }
+}
+
+// Fixed-width Amul rows, software-pipelined: the loads of a round (entries,
+// x_p, d_p: none depends on an earlier result) are issued before the
+// previous round's gathers, so each round costs about one memory round trip
+// instead of two.  For rows of at most G entries (a whole row per round).
+template <class T, int R, int G>
+struct EllRound {
+    int c[R][G];
+    T a[R][G];
+    T xp[R], d[R];
+};
+
+template <class T, int R, int G>
+__device__ __forceinline__ void ell_load(EllRound<T, R, G>& e, const Mat<T>& A, const T* x, int pb, int stride, int n)
+{
+#pragma unroll
+    for (int k = 0; k < R; k++) {
+        const int p = pb + k * stride;
+        const bool ok = p < n;
+        e.xp[k] = ok ? x[p] : T(0);
+        e.d[k] = ok ? A.d[p] : T(0);
+#pragma unroll
+        for (int j = 0; j < G; j++) {
+            const bool okj = ok && j < A.ell_w;
+            const size_t idx = (size_t)j * A.ell_stride + p;
+            e.c[k][j] = okj ? __ldg(A.Ecol + idx) : -1;
+            e.a[k][j] = okj ? A.Ea[idx] : T(0);
+        }
+    }
+}
+
+template <class T, int R, int G>
+__device__ __forceinline__ void ell_finish(const EllRound<T, R, G>& e, const Mat<T>& A, const T* x, T (&y)[R])
+{
+    T vv[R][G];
+#pragma unroll
+    for (int k = 0; k < R; k++)
+#pragma unroll
+        for (int j = 0; j < G; j++) vv[k][j] = e.c[k][j] >= 0 ? x[e.c[k][j]] : T(0);
+#pragma unroll
+    for (int k = 0; k < R; k++) {
+        y[k] = mul_rn(e.d[k], e.xp[k]);
+#pragma unroll
+        for (int j = 0; j < G; j++)
+            if (e.c[k][j] >= 0) y[k] = fmadd(e.a[k][j], vv[k][j], y[k]);
+    }
+}
+
+// q = A x over rows first + j stride (j = 0, 1, ...) below n; the sink gets
+// (row, q_row, x_row) of every row.
+template <class T, int R, int G, class Sink>
+__device__ __forceinline__ void ell_amul_pipelined(const Mat<T>& A, const T* x, int first, int stride, int n,
+                                                   Sink sink)
+{
+    EllRound<T, R, G> cur, nxt;
+    ell_load<T, R, G>(cur, A, x, first, stride, n);
+    for (int pb = first; pb < n; pb += R * stride) {
+        const int pn = pb + R * stride;
+        if (pn < n) ell_load<T, R, G>(nxt, A, x, pn, stride, n);
+        T y[R];
+        ell_finish<T, R, G>(cur, A, x, y);
+#pragma unroll
+        for (int k = 0; k < R; k++)
+            if (pb + k * stride < n) sink(pb + k * stride, y[k], cur.xp[k]);
+        cur = nxt;
     }
 }
 
@@ -549,6 +628,13 @@ __device__ bool amul_sigma(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const
     constexpr int R = AmulShape<T>::R, G = AmulShape<T>::G;
     Acc<T> asig;
     RowIter it = rows_of(g);
+    if (PipeShape<T>::in_solver && A.ell_w > 0 && A.ell_w <= PipeShape<T>::G) {
+        ell_amul_pipelined<T, PipeShape<T>::R, PipeShape<T>::G>(A, v.p, it.first, it.stride, a.n,
+                                                                [&](int p, T y, T xp) {
+                                                                    v.q[p] = y;
+                                                                    asig.prod(y, xp);
+                                                                });
+    } else
     for (int pb = it.first; pb < a.n; pb += R * it.stride) {
         int p[R];
         T y[R], pp[R];
@@ -984,6 +1070,11 @@ __global__ void __launch_bounds__(256) k_amul_prepared(int n, Mat<T> A, const T*
 {
     constexpr int R = AmulShape<T>::R, G = AmulShape<T>::G;
     const int stride = gridDim.x * blockDim.x;
+    if (PipeShape<T>::stand_alone && A.ell_w > 0 && A.ell_w <= PipeShape<T>::G) {
+        ell_amul_pipelined<T, PipeShape<T>::R, PipeShape<T>::G>(A, x, blockIdx.x * blockDim.x + threadIdx.x, stride, n,
+                                                                [&](int p, T yv, T) { y[p] = yv; });
+        return;
+    }
     for (int pb = blockIdx.x * blockDim.x + threadIdx.x; pb < n; pb += R * stride) {
         int p[R];
         T yy[R], xp[R];
