@@ -55,6 +55,9 @@ def _declare(L):
     L.oracle_assemble_laplacian.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _i32,
                                             _i32p, _f64p, _f64p, _f64p, _i8p, _f64p, _f64p]
     L.oracle_assemble_laplacian.restype = None
+    L.oracle_assembly_adjoint.argtypes = [_i32, _i32p, _i32p, _f64p, _f64p, _i32, _i32p, _f64p, _f64p, _i8p,
+                                          _f64p, _f64p, _f64p, _f64p]
+    L.oracle_assembly_adjoint.restype = None
     L.oracle_amul.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
     L.oracle_amul.restype = None
     L.oracle_amul_f32.argtypes = [_i32, _i32, _i32p, _i32p, _f32p, _f32p, _f32p, _f32p]
@@ -98,6 +101,20 @@ def assemble_laplacian(mesh, gamma, bgamma, btype):
                                     _c(mesh.bface_cf, np.float64), _c(bgamma, np.float64),
                                     _c(btype, np.int8), upper, diag)
     return upper, diag
+
+
+def assembly_adjoint(mesh, gupper, gdiag, btype):
+    """(dL/dgamma[F], dL/dbgamma[B]) from dL/dupper and dL/ddiag through the
+    assembly above (geometry fixed): the reverse mode of a2, which is linear
+    in the diffusivities."""
+    gg = np.empty(mesh.n_faces)
+    gb = np.empty(mesh.n_bfaces)
+    lib().oracle_assembly_adjoint(mesh.n_faces, _c(mesh.lower, np.int32), _c(mesh.upper_addr, np.int32),
+                                  _c(mesh.sf, np.float64), _c(mesh.c, np.float64), mesh.n_bfaces,
+                                  _c(mesh.bface_cell, np.int32), _c(mesh.bface_sf, np.float64),
+                                  _c(mesh.bface_cf, np.float64), _c(btype, np.int8), _c(gupper, np.float64),
+                                  _c(gdiag, np.float64), gg, gb)
+    return gg, gb
 
 
 def amul(l, u, diag, upper, x):

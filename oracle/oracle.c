@@ -67,6 +67,35 @@ void oracle_assemble_laplacian(int32_t n_cells, int32_t n_faces, const int32_t* 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Reverse mode of the assembly above with respect to the diffusivities,     */
+/* the geometry held fixed.  a_f is linear in gamma_f:                       */
+/*   d a_f / d gamma_f = |S_f| / max(n.d, 0.05 |d|)  (face_coeff at gamma 1) */
+/* and a_f enters upper_f with sign -1 and diag_l, diag_u with sign +1, a_b  */
+/* (Dirichlet) enters diag of its cell.  Given gu = dL/dupper, gd = dL/ddiag:*/
+/*   dL/dgamma_f = ((gd_l + gd_u) - gu_f) * (d a_f / d gamma_f)             */
+/*   dL/dbgamma_b = gd_cell * (d a_b / d gamma_b)  (Dirichlet), 0 otherwise  */
+/* ------------------------------------------------------------------------ */
+void oracle_assembly_adjoint(int32_t n_faces, const int32_t* l, const int32_t* u, const double* sf,
+                             const double* c, int32_t n_b, const int32_t* bcell, const double* bsf,
+                             const double* bcf, const int8_t* btype, const double* gu, const double* gd,
+                             double* ggamma, double* gbgamma)
+{
+    for (int32_t f = 0; f < n_faces; f++) {
+        double da = face_coeff(sf + 3 * (int64_t)f, c + 3 * (int64_t)l[f], c + 3 * (int64_t)u[f], 1.0);
+        ggamma[f] = ((gd[l[f]] + gd[u[f]]) - gu[f]) * da;
+    }
+    for (int32_t b = 0; b < n_b; b++) {
+        if (btype[b] != 1) {
+            gbgamma[b] = 0.0;
+            continue;
+        }
+        int32_t i = bcell[b];
+        double da = face_coeff(bsf + 3 * (int64_t)b, c + 3 * (int64_t)i, bcf + 3 * (int64_t)b, 1.0);
+        gbgamma[b] = gd[i] * da;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* lduMatrix::Amul (paper Sec. 4.2 profiling table, "SpMVM (Amul + Tmul)"):   */
 /*   y_i = d_i x_i, then for each face f ascending:                          */
 /*   y_u += a_f x_l ; y_l += a_f x_u   (each += one fused multiply-add)      */

@@ -368,6 +368,83 @@ def test_adjoint_finite_differences():
         assert fd_u == pytest.approx(np.dot(du, vu), rel=1e-6)
 
 
+# ------------------------------------------------ assembly adjoint (dL/dgamma) ----
+def _assembly_grads(c, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(c.mesh.n_faces), rng.standard_normal(c.mesh.n_cells)
+
+
+def test_assembly_adjoint_homogeneity():
+    """upper and diag are homogeneous of degree one in (gamma, bgamma), so
+    gamma.dL/dgamma + bgamma.dL/dbgamma = upper.dL/dupper + diag.dL/ddiag."""
+    c, up, dg = case(6, jitter=0.2, permute=True, seed=31, lognormal_gamma=True)
+    gu, gd = _assembly_grads(c, 32)
+    gg, gb = oracle.assembly_adjoint(c.mesh, gu, gd, c.btype)
+    lhs = np.dot(gg, c.gamma) + np.dot(gb, c.bgamma)
+    assert lhs == pytest.approx(np.dot(gu, up) + np.dot(gd, dg), rel=1e-12)
+
+
+def test_assembly_adjoint_directional_derivative():
+    """The assembly is linear in the diffusivities: a central difference of
+    phi = dL/dupper.upper + dL/ddiag.diag along any direction is exact up to
+    rounding, and equals the adjoint's directional derivative."""
+    c, up, dg = case((5, 4, 3), jitter=0.2, permute=True, seed=33, lognormal_gamma=True)
+    m = c.mesh
+    gu, gd = _assembly_grads(c, 34)
+    gg, gb = oracle.assembly_adjoint(m, gu, gd, c.btype)
+    rng = np.random.default_rng(35)
+    for _ in range(4):
+        vg = rng.standard_normal(m.n_faces) * c.gamma
+        vb = rng.standard_normal(m.n_bfaces) * c.bgamma
+
+        def phi(t):
+            u1, d1 = oracle.assemble_laplacian(m, c.gamma + t * vg, c.bgamma + t * vb, c.btype)
+            return np.dot(gu, u1) + np.dot(gd, d1)
+
+        fd = (phi(0.5) - phi(-0.5)) / 1.0
+        assert fd == pytest.approx(np.dot(gg, vg) + np.dot(gb, vb), rel=1e-9)
+    # zero-gradient faces get no gradient, Dirichlet faces do
+    assert np.all(gb[c.btype != 1] == 0.0) and np.any(gb[c.btype == 1] != 0.0)
+
+
+def test_assembly_adjoint_uniform_closed_form():
+    """Uniform cubes of side h: d a_f / d gamma_f = |S| / |d| = h for internal
+    faces and h^2 / (h/2) = 2h for Dirichlet faces."""
+    n = 4
+    c, up, dg = case(n, seed=36)
+    m = c.mesh
+    h = 1.0 / n
+    gu, gd = _assembly_grads(c, 37)
+    gg, gb = oracle.assembly_adjoint(m, gu, gd, c.btype)
+    assert np.allclose(gg, ((gd[m.lower] + gd[m.upper_addr]) - gu) * h, rtol=1e-12, atol=0)
+    dir_ = c.btype == 1
+    assert np.allclose(gb[dir_], gd[m.bface_cell[dir_]] * 2 * h, rtol=1e-12, atol=0)
+
+
+def test_gamma_gradient_through_solve_finite_differences():
+    """L(gamma) = 0.5 |x(gamma) - x_t|^2 with A(gamma) x = b: the solve's
+    adjoint followed by the assembly's against central differences."""
+    c = hexmesh.pressure_case(4, jitter=0.2, permute=True, seed=38, lognormal_gamma=True, with_target=True)
+    m = c.mesh
+    args = (m.lower, m.upper_addr)
+
+    def loss(gamma, bgamma):
+        up, dg = oracle.assemble_laplacian(m, gamma, bgamma, c.btype)
+        x, _ = oracle.pcg(*args, dg, up, c.b, tol=1e-15, max_iter=5000)
+        return 0.5 * np.sum((x - c.x_t) ** 2), x, up, dg
+
+    L0, x, up, dg = loss(c.gamma, c.bgamma)
+    _, du, dd, _ = oracle.adjoint(*args, dg, up, x, x - c.x_t, tol=1e-15)
+    gg, gb = oracle.assembly_adjoint(m, du, dd, c.btype)
+    rng = np.random.default_rng(39)
+    h = 1e-6
+    for _ in range(4):
+        vg = rng.standard_normal(m.n_faces) * c.gamma
+        vb = rng.standard_normal(m.n_bfaces) * c.bgamma
+        fd = (loss(c.gamma + h * vg, c.bgamma + h * vb)[0] - loss(c.gamma - h * vg, c.bgamma - h * vb)[0]) / (2 * h)
+        assert fd == pytest.approx(np.dot(gg, vg) + np.dot(gb, vb), rel=1e-6)
+
+
 def test_pcg_norm_factor_shift_invariance():
     """With zero row sums (all-Neumann boundary) A (x + c) - s (xbar + c) = A x - s xbar
     for every constant c, so the normalisation factor does not depend on the
