@@ -153,6 +153,22 @@ spuma_status spuma_assemble_laplacian(spuma_ldu_t h, const double* face_sf, cons
                                       const double* bface_cf, const double* bface_gamma,
                                       const int8_t* bface_type, double* upper, double* diag,
                                       spuma_stream_t stream);
+/* Reverse mode of the assembly above with respect to the diffusivities, the
+ * geometry held fixed (an extension of the paper's method: the chain from
+ * the solve's adjoint, spuma_pcg_adjoint, to gamma).  a_f is linear in
+ * gamma_f with d a_f / d gamma_f = |S_f| / max(n_f . d_f, 0.05 |d_f|), so
+ *   dldgamma_f  = ((dlddiag_{l(f)} + dlddiag_{u(f)}) - dldupper_f) * d a_f / d gamma_f,
+ *   dldbgamma_b = dlddiag_{cell(b)} * d a_b / d gamma_b  (Dirichlet faces), 0 (zero gradient).
+ * Same geometry arrays and layout as the assembly; dldupper[F], dlddiag[N]
+ * in, dldgamma[F] and dldbgamma[B] out (FP64, original order; dldbgamma may
+ * be NULL, and so may the boundary arrays when n_bfaces is 0).  One kernel
+ * per face set, no atomics: each output element is written once. */
+spuma_status spuma_assemble_laplacian_adjoint(spuma_ldu_t h, const double* face_sf, const double* cell_c,
+                                              int32_t n_bfaces, const int32_t* bface_cell,
+                                              const double* bface_sf, const double* bface_cf,
+                                              const int8_t* bface_type, const double* dldupper,
+                                              const double* dlddiag, double* dldgamma, double* dldbgamma,
+                                              spuma_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * lduMatrix::Amul (paper Sec. 4.2, profiling table "SpMVM (Amul + Tmul)"):

@@ -4,8 +4,9 @@ kernels behind a C ABI (include/spuma.h)."""
 from ._lib import (F32, F64, MIXED, MIXED_RESTART, PRECOND_DIAGONAL, PRECOND_DIC, PRECOND_NONE, Controls, Perf,
                    SpumaError, lib)
 from .core import LduMesh, SolverControls, BatchSolve, solve_host
-from .autograd import PressureSolve, pressure_solve
+from .autograd import LaplacianAssembly, PressureSolve, assemble_laplacian, pressure_solve
 
-__all__ = ["LduMesh", "SolverControls", "BatchSolve", "PressureSolve", "pressure_solve", "solve_host",
+__all__ = ["LduMesh", "SolverControls", "BatchSolve", "PressureSolve", "pressure_solve", "LaplacianAssembly",
+           "assemble_laplacian", "solve_host",
            "Controls", "Perf", "SpumaError", "lib", "F64", "F32", "MIXED", "MIXED_RESTART", "PRECOND_NONE",
            "PRECOND_DIAGONAL", "PRECOND_DIC"]

@@ -55,6 +55,7 @@ _SIGS = {
     "spuma_ldu_info": (_I, [_H, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "spuma_ldu_device_status": (_I, [_H, _P]),
     "spuma_assemble_laplacian": (_I, [_H, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "spuma_assemble_laplacian_adjoint": (_I, [_H, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "spuma_amul": (_I, [_H, _I, _P, _P, _P, _P, _P]),
     "spuma_matrix_prepare": (_I, [_H, _P, _P, _I, _P]),
     "spuma_read_rD": (_I, [_H, _P, _P]),

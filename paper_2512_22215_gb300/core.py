@@ -94,6 +94,19 @@ class LduMesh:
                                              ptr(upper), ptr(diag), stream_ptr()), "spuma_assemble_laplacian")
         return upper, diag
 
+    def assemble_laplacian_adjoint(self, sf, c, dl_dupper, dl_ddiag, bface_cell=None, bface_sf=None, bface_cf=None,
+                                   btype=None):
+        """(dL/dgamma[F], dL/dbgamma[B] or None) from dL/dupper and dL/ddiag."""
+        gg = torch.empty(self.n_faces, dtype=torch.float64, device=self.device)
+        nb = 0 if bface_cell is None else int(bface_cell.numel())
+        gb = torch.empty(nb, dtype=torch.float64, device=self.device) if nb else None
+        check(lib().spuma_assemble_laplacian_adjoint(self.handle, ptr(sf), ptr(c), nb, ptr(bface_cell),
+                                                     ptr(bface_sf), ptr(bface_cf), ptr(btype),
+                                                     ptr(dl_dupper.contiguous()), ptr(dl_ddiag.contiguous()),
+                                                     ptr(gg), ptr(gb), stream_ptr()),
+              "spuma_assemble_laplacian_adjoint")
+        return gg, gb
+
     def amul(self, diag, upper, x, out=None):
         prec = F32 if x.dtype == torch.float32 else F64
         y = out if out is not None else torch.empty_like(x)

@@ -48,6 +48,41 @@ __global__ void k_face_coeff(int nf, const int* __restrict__ l, const int* __res
     }
 }
 
+// Reverse mode of the assembly with respect to gamma: d a / d gamma is the
+// face coefficient at gamma = 1 (a is linear in gamma).
+__global__ void k_gamma_grad(int nf, const int* __restrict__ l, const int* __restrict__ u,
+                             const double* __restrict__ sf, const double* __restrict__ c,
+                             const double* __restrict__ gu, const double* __restrict__ gd, double* gg)
+{
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+        const double* s = sf + 3 * (size_t)f;
+        const double* cl = c + 3 * (size_t)l[f];
+        const double* cu = c + 3 * (size_t)u[f];
+        const double da = face_coeff(s[0], s[1], s[2], __dsub_rn(cu[0], cl[0]), __dsub_rn(cu[1], cl[1]),
+                                     __dsub_rn(cu[2], cl[2]), 1.0);
+        gg[f] = __dmul_rn(__dsub_rn(__dadd_rn(gd[l[f]], gd[u[f]]), gu[f]), da);
+    }
+}
+
+__global__ void k_bgamma_grad(int nb, const int* __restrict__ bcell, const int8_t* __restrict__ btype,
+                              const double* __restrict__ bsf, const double* __restrict__ bcf,
+                              const double* __restrict__ c, const double* __restrict__ gd, double* gb)
+{
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        if (btype[b] != 1) {
+            gb[b] = 0.0;
+            continue;
+        }
+        const int i = bcell[b];
+        const double* s = bsf + 3 * (size_t)b;
+        const double* cb = bcf + 3 * (size_t)b;
+        const double* ci = c + 3 * (size_t)i;
+        const double da = face_coeff(s[0], s[1], s[2], __dsub_rn(cb[0], ci[0]), __dsub_rn(cb[1], ci[1]),
+                                     __dsub_rn(cb[2], ci[2]), 1.0);
+        gb[b] = __dmul_rn(gd[i], da);
+    }
+}
+
 __global__ void k_bcount(int nb, const int* __restrict__ bcell, const int8_t* __restrict__ btype, int* cnt)
 {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x)
@@ -178,6 +213,35 @@ spuma_status spuma_assemble_laplacian(spuma_ldu_t h, const double* face_sf, cons
         SPUMA_CUDA(cudaMemsetAsync(diag, 0, 8 * (size_t)h->n, s));
     }
     count_launch();
+    SPUMA_CUDA(cudaGetLastError());
+    return SPUMA_OK;
+}
+
+spuma_status spuma_assemble_laplacian_adjoint(spuma_ldu_t h, const double* face_sf, const double* cell_c,
+                                              int32_t n_bfaces, const int32_t* bface_cell, const double* bface_sf,
+                                              const double* bface_cf, const int8_t* bface_type,
+                                              const double* dldupper, const double* dlddiag, double* dldgamma,
+                                              double* dldbgamma, spuma_stream_t stream)
+{
+    if (!h || n_bfaces < 0 || (h->n > 0 && (!cell_c || !dlddiag)) ||
+        (h->nf > 0 && (!face_sf || !dldupper || !dldgamma)) ||
+        (n_bfaces > 0 && dldbgamma && (!bface_cell || !bface_sf || !bface_cf || !bface_type))) {
+        set_error("spuma_assemble_laplacian_adjoint: bad argument");
+        return SPUMA_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int T = 256;
+    const Layout& L = h->L;
+    if (h->nf > 0) {
+        k_gamma_grad<<<grid1d(h->nf, T, h->num_sms), T, 0, s>>>(h->nf, h->at<int>(L.laddr), h->at<int>(L.uaddr),
+                                                                face_sf, cell_c, dldupper, dlddiag, dldgamma);
+        count_launch();
+    }
+    if (n_bfaces > 0 && dldbgamma) {
+        k_bgamma_grad<<<grid1d(n_bfaces, T, h->num_sms), T, 0, s>>>(n_bfaces, bface_cell, bface_type, bface_sf,
+                                                                    bface_cf, cell_c, dlddiag, dldbgamma);
+        count_launch();
+    }
     SPUMA_CUDA(cudaGetLastError());
     return SPUMA_OK;
 }
