@@ -58,6 +58,19 @@ def _declare(L):
     L.oracle_assembly_adjoint.argtypes = [_i32, _i32p, _i32p, _f64p, _f64p, _i32, _i32p, _f64p, _f64p, _i8p,
                                           _f64p, _f64p, _f64p, _f64p]
     L.oracle_assembly_adjoint.restype = None
+    L.oracle_fv_weights.argtypes = [_i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
+    L.oracle_fv_weights.restype = None
+    L.oracle_fv_grad.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _i32, _i32p, _f64p, _i8p, _f64p,
+                                 _f64p]
+    L.oracle_fv_grad.restype = None
+    L.oracle_pressure_rhs.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _i32,
+                                      _i32p, _f64p, _f64p, _f64p]
+    L.oracle_pressure_rhs.restype = None
+    L.oracle_pressure_flux.argtypes = [_i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _i32, _i32p, _f64p, _f64p,
+                                       _f64p, _i8p, _f64p, _f64p, _f64p, _f64p]
+    L.oracle_pressure_flux.restype = None
+    L.oracle_fv_div.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _i32, _i32p, _f64p, _f64p]
+    L.oracle_fv_div.restype = None
     L.oracle_amul.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
     L.oracle_amul.restype = None
     L.oracle_amul_f32.argtypes = [_i32, _i32, _i32p, _i32p, _f32p, _f32p, _f32p, _f32p]
@@ -115,6 +128,57 @@ def assembly_adjoint(mesh, gupper, gdiag, btype):
                                   _c(mesh.bface_cf, np.float64), _c(btype, np.int8), _c(gupper, np.float64),
                                   _c(gdiag, np.float64), gg, gb)
     return gg, gb
+
+
+# ---------------------------------------------- pressure-correction step ----
+def fv_weights(mesh):
+    """Linear interpolation weight of the owner value at each internal face."""
+    w = np.empty(mesh.n_faces)
+    lib().oracle_fv_weights(mesh.n_faces, _c(mesh.lower, np.int32), _c(mesh.upper_addr, np.int32),
+                            _c(mesh.sf, np.float64), _c(mesh.cf, np.float64), _c(mesh.c, np.float64), w)
+    return w
+
+
+def fv_grad(mesh, w, btype, p):
+    """Gauss linear gradient [N, 3] (Dirichlet faces p = 0, zero-gradient p_b = p_cell)."""
+    g = np.empty((mesh.n_cells, 3))
+    lib().oracle_fv_grad(mesh.n_cells, mesh.n_faces, _c(mesh.lower, np.int32), _c(mesh.upper_addr, np.int32),
+                         _c(mesh.sf, np.float64), _c(w, np.float64), _c(mesh.v, np.float64), mesh.n_bfaces,
+                         _c(mesh.bface_cell, np.int32), _c(mesh.bface_sf, np.float64), _c(btype, np.int8),
+                         _c(p, np.float64), g)
+    return g
+
+
+def pressure_rhs(mesh, w, gamma, grad, phi, bphi):
+    """(corr[F], b[N]): explicit non-orthogonal correction flux and the
+    right-hand side of A p = b for laplacian(gamma, p) = div(phiHbyA)."""
+    corr = np.empty(mesh.n_faces)
+    b = np.empty(mesh.n_cells)
+    lib().oracle_pressure_rhs(mesh.n_cells, mesh.n_faces, _c(mesh.lower, np.int32), _c(mesh.upper_addr, np.int32),
+                              _c(mesh.sf, np.float64), _c(mesh.c, np.float64), _c(w, np.float64),
+                              _c(gamma, np.float64), _c(grad, np.float64), _c(phi, np.float64), mesh.n_bfaces,
+                              _c(mesh.bface_cell, np.int32), _c(bphi, np.float64), corr, b)
+    return corr, b
+
+
+def pressure_flux(mesh, upper, corr, p, phi, bgamma, btype, bphi):
+    """(phi[F], bphi[B]) after the solve."""
+    out = np.empty(mesh.n_faces)
+    bout = np.empty(mesh.n_bfaces)
+    lib().oracle_pressure_flux(mesh.n_faces, _c(mesh.lower, np.int32), _c(mesh.upper_addr, np.int32),
+                               _c(upper, np.float64), _c(corr, np.float64), _c(p, np.float64), _c(phi, np.float64),
+                               mesh.n_bfaces, _c(mesh.bface_cell, np.int32), _c(mesh.bface_sf, np.float64),
+                               _c(mesh.bface_cf, np.float64), _c(bgamma, np.float64), _c(btype, np.int8),
+                               _c(mesh.c, np.float64), _c(bphi, np.float64), out, bout)
+    return out, bout
+
+
+def fv_div(mesh, phi, bphi):
+    """Integrated divergence [N] of face and boundary fluxes."""
+    d = np.empty(mesh.n_cells)
+    lib().oracle_fv_div(mesh.n_cells, mesh.n_faces, _c(mesh.lower, np.int32), _c(mesh.upper_addr, np.int32),
+                        _c(phi, np.float64), mesh.n_bfaces, _c(mesh.bface_cell, np.int32), _c(bphi, np.float64), d)
+    return d
 
 
 def amul(l, u, diag, upper, x):

@@ -541,3 +541,127 @@ done:
     free(w); free(p); free(q); free(rD32);
     return status;
 }
+
+/* ======================================================================== */
+/* Pressure-correction step around the solve (the paper's SIMPLE loop with  */
+/* the schemes of its fvSchemes listing: gradSchemes Gauss linear,          */
+/* interpolationSchemes linear, laplacianSchemes Gauss linear corrected,    */
+/* snGradSchemes corrected; fvSolution: nNonOrthogonalCorrectors 0).  All   */
+/* integrated over the cell (no division by volume except the gradient).    */
+/* Boundary: Dirichlet faces carry p = 0, zero-gradient faces p_b = p_cell. */
+/* ======================================================================== */
+
+/* Linear interpolation weight of the owner (l) value at face f:             */
+/*   w_f = |S.(C_u - C_f)| / (|S.(C_f - C_l)| + |S.(C_u - C_f)|),            */
+/*   p_f = w_f p_l + (1 - w_f) p_u.                                          */
+void oracle_fv_weights(int32_t nf, const int32_t* l, const int32_t* u, const double* sf, const double* cf,
+                       const double* c, double* w)
+{
+    for (int32_t f = 0; f < nf; f++) {
+        const double* s = sf + 3 * (int64_t)f;
+        const double* x = cf + 3 * (int64_t)f;
+        const double* cl = c + 3 * (int64_t)l[f];
+        const double* cu = c + 3 * (int64_t)u[f];
+        double own = fabs((s[0] * (x[0] - cl[0]) + s[1] * (x[1] - cl[1])) + s[2] * (x[2] - cl[2]));
+        double nei = fabs((s[0] * (cu[0] - x[0]) + s[1] * (cu[1] - x[1])) + s[2] * (cu[2] - x[2]));
+        w[f] = nei / (own + nei);
+    }
+}
+
+/* Gauss linear gradient: grad_i = (1/V_i) sum over the faces of i of       */
+/* S_f p_f (S outward: +S_f for the owner, -S_f for the neighbour), faces   */
+/* in ascending order, then the boundary faces of i in ascending order.     */
+void oracle_fv_grad(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, const double* sf,
+                    const double* w, const double* v, int32_t n_b, const int32_t* bcell, const double* bsf,
+                    const int8_t* btype, const double* p, double* grad)
+{
+    for (int64_t k = 0; k < 3 * (int64_t)n; k++) grad[k] = 0.0;
+    for (int32_t f = 0; f < nf; f++) {
+        const double pf = w[f] * p[l[f]] + (1.0 - w[f]) * p[u[f]];
+        for (int d = 0; d < 3; d++) {
+            const double t = sf[3 * (int64_t)f + d] * pf;
+            grad[3 * (int64_t)l[f] + d] += t;
+            grad[3 * (int64_t)u[f] + d] -= t;
+        }
+    }
+    for (int32_t b = 0; b < n_b; b++) {
+        const int32_t i = bcell[b];
+        const double pb = btype[b] == 1 ? 0.0 : p[i];
+        for (int d = 0; d < 3; d++) grad[3 * (int64_t)i + d] += bsf[3 * (int64_t)b + d] * pb;
+    }
+    for (int32_t i = 0; i < n; i++)
+        for (int d = 0; d < 3; d++) grad[3 * (int64_t)i + d] /= v[i];
+}
+
+/* Explicit non-orthogonal correction flux of the corrected laplacian and   */
+/* the pressure right-hand side.  Per internal face:                        */
+/*   |S| = sqrt((Sx Sx + Sy Sy) + Sz Sz), d = C_u - C_l, |d| likewise,        */
+/*   n.d = ((Sx dx + Sy dy) + Sz dz)/|S|, delta = 1/max(n.d, 0.05 |d|),       */
+/*   k = S/|S| - d delta  (the correction vector),                           */
+/*   (grad p)_f = w grad_l + (1 - w) grad_u  (componentwise),                */
+/*   corr_f = (gamma_f |S|) ((k_x g_x + k_y g_y) + k_z g_z).                  */
+/* With A = -laplacian (implicit part) the pressure equation                 */
+/*   laplacian(gamma, p) = div(phiHbyA) reads A p = b with                   */
+/*   b_i = sum_f +-(corr_f - phi_f) (+ owner, - neighbour, faces ascending)  */
+/*         - sum of phi_b over the boundary faces of i (ascending).          */
+void oracle_pressure_rhs(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, const double* sf,
+                         const double* c, const double* w, const double* gamma, const double* grad,
+                         const double* phi, int32_t n_b, const int32_t* bcell, const double* bphi,
+                         double* corr, double* b)
+{
+    for (int32_t i = 0; i < n; i++) b[i] = 0.0;
+    for (int32_t f = 0; f < nf; f++) {
+        const double* s = sf + 3 * (int64_t)f;
+        const double* cl = c + 3 * (int64_t)l[f];
+        const double* cu = c + 3 * (int64_t)u[f];
+        const double* gl = grad + 3 * (int64_t)l[f];
+        const double* gu = grad + 3 * (int64_t)u[f];
+        double dx = cu[0] - cl[0], dy = cu[1] - cl[1], dz = cu[2] - cl[2];
+        double mags = sqrt((s[0] * s[0] + s[1] * s[1]) + s[2] * s[2]);
+        double magd = sqrt((dx * dx + dy * dy) + dz * dz);
+        double ndotd = ((s[0] * dx + s[1] * dy) + s[2] * dz) / mags;
+        double delta = 1.0 / fmax(ndotd, 0.05 * magd);
+        double kx = s[0] / mags - dx * delta, ky = s[1] / mags - dy * delta, kz = s[2] / mags - dz * delta;
+        double wf = w[f], wu = 1.0 - w[f];
+        double gx = wf * gl[0] + wu * gu[0], gy = wf * gl[1] + wu * gu[1], gz = wf * gl[2] + wu * gu[2];
+        corr[f] = (gamma[f] * mags) * ((kx * gx + ky * gy) + kz * gz);
+        const double t = corr[f] - phi[f];
+        b[l[f]] += t;
+        b[u[f]] -= t;
+    }
+    for (int32_t k = 0; k < n_b; k++) b[bcell[k]] -= bphi[k];
+}
+
+/* Flux after the solve: phi_f = phiHbyA_f - (a_f (p_u - p_l) + corr_f),     */
+/* a_f = -upper_f; boundary: Dirichlet phi_b = phiHbyA_b + a_b p_cell with   */
+/* a_b the boundary coefficient of the assembly, zero-gradient phiHbyA_b.   */
+void oracle_pressure_flux(int32_t nf, const int32_t* l, const int32_t* u, const double* upper,
+                          const double* corr, const double* p, const double* phi, int32_t n_b,
+                          const int32_t* bcell, const double* bsf, const double* bcf, const double* bgamma,
+                          const int8_t* btype, const double* c, const double* bphi, double* phi_out,
+                          double* bphi_out)
+{
+    for (int32_t f = 0; f < nf; f++) phi_out[f] = phi[f] - ((-upper[f]) * (p[u[f]] - p[l[f]]) + corr[f]);
+    for (int32_t b = 0; b < n_b; b++) {
+        if (btype[b] != 1) {
+            bphi_out[b] = bphi[b];
+            continue;
+        }
+        const int32_t i = bcell[b];
+        const double ab = face_coeff(bsf + 3 * (int64_t)b, c + 3 * (int64_t)i, bcf + 3 * (int64_t)b, bgamma[b]);
+        bphi_out[b] = bphi[b] + ab * p[i];
+    }
+}
+
+/* Integrated divergence: div_i = sum_f +-phi_f (+ owner, - neighbour, faces */
+/* ascending) + the boundary fluxes of i (ascending).                        */
+void oracle_fv_div(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, const double* phi, int32_t n_b,
+                   const int32_t* bcell, const double* bphi, double* div)
+{
+    for (int32_t i = 0; i < n; i++) div[i] = 0.0;
+    for (int32_t f = 0; f < nf; f++) {
+        div[l[f]] += phi[f];
+        div[u[f]] -= phi[f];
+    }
+    for (int32_t b = 0; b < n_b; b++) div[bcell[b]] += bphi[b];
+}
