@@ -387,6 +387,35 @@ def main():
     amul64_us = time_amul(xi, yi)
     amul32_us = time_amul(xi32, yi32)
 
+    # the pressure-correction step's explicit operators around the solve
+    # (gradient, corrected-laplacian RHS, flux reconstruction, divergence)
+    def time_op(fn, reps=20):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a_, c_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(s)
+        for _ in range(reps):
+            fn()
+        c_.record(s)
+        c_.synchronize()
+        return a_.elapsed_time(c_) / reps * 1e3   # us
+
+    rng_ps = np.random.default_rng(7)
+    cf_d, v_d = T(m.cf), T(m.v)
+    phi_d = T(rng_ps.standard_normal(F) * np.linalg.norm(m.sf, axis=1))
+    bphi_d = T(rng_ps.standard_normal(m.n_bfaces) * np.linalg.norm(m.bface_sf, axis=1))
+    w_d = M.fv_weights(sf, cf_d, cc)
+    g_d = M.fv_grad(sf, w_d, v_d, b, bcell, bsf, bt)
+    corr_d, rhs_d = M.pressure_rhs(sf, cc, w_d, gamma, g_d, phi_d, bcell, bphi_d)
+    B = m.n_bfaces
+    ps_us = {"grad": time_op(lambda: M.fv_grad(sf, w_d, v_d, b, bcell, bsf, bt)),
+             "rhs": time_op(lambda: M.pressure_rhs(sf, cc, w_d, gamma, g_d, phi_d, bcell, bphi_d)),
+             "flux": time_op(lambda: M.pressure_flux(up, corr_d, b, phi_d, cc, bcell, bsf, bcf, bg, bt, bphi_d)),
+             "div": time_op(lambda: M.fv_div(phi_d, bcell, bphi_d))}
+    ps_bytes = {"grad": 40 * F + 40 * N + 29 * B, "rhs": 72 * F + 56 * N + 12 * B,
+                "flux": 40 * F + 8 * N + 77 * B, "div": 8 * F + 8 * N + 12 * B}
+
     # ----------------------------------------------------- end to end (host)
     gamma_h = torch.from_numpy(case.gamma).pin_memory()
     b_h = torch.from_numpy(case.b).pin_memory()
@@ -445,6 +474,12 @@ def main():
                  "f64_frac_ldu": round(wb["amul64"] / amul64_us / 1e3 / hbm, 4),
                  "f32_us": round(amul32_us, 2), "f32_gbs_ldu": round(wb["amul32"] / amul32_us / 1e3, 1),
                  "basis": "LDU algorithmic bytes 16F + 24N (FP64), 12F + 12N (FP32)"},
+        "pressure_step": dict(
+            **{f"{k}_us": round(v, 2) for k, v in ps_us.items()},
+            **{f"{k}_gbs": round(ps_bytes[k] / ps_us[k] / 1e3, 1) for k in ps_us},
+            basis="algorithmic bytes, int32 indices: grad 40F + 40N + 29B, rhs 72F + 56N + 12B, "
+                  "flux 40F + 8N + 77B, div 8F + 8N + 12B (B boundary faces); each call builds its "
+                  "per-cell boundary-face lists"),
         "n_levels": M.n_levels,
         "roofline": roofline,
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

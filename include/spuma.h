@@ -264,6 +264,54 @@ spuma_status spuma_pcg_solve_static(int32_t n_cells, int32_t n_faces, const int3
                                     spuma_solver_perf* perf, spuma_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * The pressure-correction step around the solve (the paper's SIMPLE loop
+ * with the schemes of its fvSchemes listing: gradSchemes Gauss linear,
+ * interpolationSchemes linear, laplacianSchemes Gauss linear corrected,
+ * snGradSchemes corrected; nNonOrthogonalCorrectors 0 in its fvSolution).
+ * All quantities are integrated over the cell (no division by volume except
+ * in the gradient); original order, FP64; the geometry arrays are those of
+ * spuma_assemble_laplacian plus face_cf[F][3] (internal face centres) and
+ * cell_v[N] (volumes); boundary faces: Dirichlet (type 1) carry p = 0,
+ * zero-gradient (type 0) p_b = p_cell.  Every per-cell result is a gather in
+ * ascending face order, then the cell's boundary faces in ascending order:
+ * bit-identical to the sequential face loop.  These calls use the handle's
+ * vector region as scratch (as the assembly does): do not overlap them with
+ * a solve on the same handle.
+ *
+ * spuma_fv_weights: w[F], the owner weight of the linear interpolation
+ *   p_f = w p_l + (1 - w) p_u, w = |S.(C_u - C_f)| / (|S.(C_f - C_l)| + |S.(C_u - C_f)|).
+ * spuma_fv_grad: grad[N][3] = (1/V_i) sum_f S_f p_f (outward S: +S_f for the
+ *   owner, -S_f for the neighbour; boundary S_b p_b).
+ * spuma_pressure_rhs: corr[F] = (gamma_f |S_f|) (k_f . (w grad_l + (1 - w) grad_u)),
+ *   the explicit non-orthogonal correction of the corrected laplacian, with
+ *   k_f = S_f/|S_f| - d_f / max(n.d, 0.05 |d|) and d_f = C_u - C_l; and
+ *   b[N] = sum_f +-(corr_f - phi_f) (+ owner, - neighbour) - sum_b phi_b, so
+ *   that laplacian(gamma, p) = div(phiHbyA) reads A p = b with the (upper,
+ *   diag) of spuma_assemble_laplacian.  phi[F], bphi[B]: phiHbyA.
+ * spuma_pressure_flux: phi_out_f = phi_f - (a_f (p_u - p_l) + corr_f), a_f =
+ *   -upper_f; bphi_out_b = bphi_b + a_b p_cell on Dirichlet faces (a_b the
+ *   assembly's boundary coefficient), bphi_b on zero-gradient ones.  With p
+ *   from A p = b the result is divergence-free to the solver tolerance.
+ * spuma_fv_div: div[N] = sum_f +-phi_f + sum_b bphi_b (integrated).
+ * ---------------------------------------------------------------------- */
+spuma_status spuma_fv_weights(spuma_ldu_t h, const double* face_sf, const double* face_cf, const double* cell_c,
+                              double* w, spuma_stream_t stream);
+spuma_status spuma_fv_grad(spuma_ldu_t h, const double* face_sf, const double* w, const double* cell_v,
+                           int32_t n_bfaces, const int32_t* bface_cell, const double* bface_sf,
+                           const int8_t* bface_type, const double* p, double* grad, spuma_stream_t stream);
+spuma_status spuma_pressure_rhs(spuma_ldu_t h, const double* face_sf, const double* cell_c, const double* w,
+                                const double* face_gamma, const double* grad, const double* phi,
+                                int32_t n_bfaces, const int32_t* bface_cell, const double* bphi, double* corr,
+                                double* b, spuma_stream_t stream);
+spuma_status spuma_pressure_flux(spuma_ldu_t h, const double* upper, const double* corr, const double* p,
+                                 const double* phi, int32_t n_bfaces, const int32_t* bface_cell,
+                                 const double* bface_sf, const double* bface_cf, const double* bface_gamma,
+                                 const int8_t* bface_type, const double* cell_c, const double* bphi,
+                                 double* phi_out, double* bphi_out, spuma_stream_t stream);
+spuma_status spuma_fv_div(spuma_ldu_t h, const double* phi, int32_t n_bfaces, const int32_t* bface_cell,
+                          const double* bphi, double* div, spuma_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * Adjoint of x = A^-1 b for a loss L(x), given x and dldx = dL/dx:
  *   A lambda = dldx (A symmetric: A^T = A, same PCG, lambda from 0);
  *   dL/db = lambda;  dL/dupper_f = -(lambda_{l(f)} x_{u(f)} + lambda_{u(f)} x_{l(f)});

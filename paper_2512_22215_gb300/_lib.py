@@ -57,6 +57,11 @@ _SIGS = {
     "spuma_assemble_laplacian": (_I, [_H, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
     "spuma_assemble_laplacian_adjoint": (_I, [_H, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "spuma_amul": (_I, [_H, _I, _P, _P, _P, _P, _P]),
+    "spuma_fv_weights": (_I, [_H, _P, _P, _P, _P, _P]),
+    "spuma_fv_grad": (_I, [_H, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P]),
+    "spuma_pressure_rhs": (_I, [_H, _P, _P, _P, _P, _P, _P, _I, _P, _P, _P, _P, _P]),
+    "spuma_pressure_flux": (_I, [_H, _P, _P, _P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "spuma_fv_div": (_I, [_H, _P, _I, _P, _P, _P, _P]),
     "spuma_matrix_prepare": (_I, [_H, _P, _P, _I, _P]),
     "spuma_read_rD": (_I, [_H, _P, _P]),
     "spuma_amul_prepared": (_I, [_H, _I, _P, _P, _P]),

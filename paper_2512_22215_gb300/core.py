@@ -107,6 +107,59 @@ class LduMesh:
               "spuma_assemble_laplacian_adjoint")
         return gg, gb
 
+    # ------------------------------------------ pressure-correction step --
+    def fv_weights(self, sf, cf, c):
+        w = torch.empty(self.n_faces, dtype=torch.float64, device=self.device)
+        check(lib().spuma_fv_weights(self.handle, ptr(sf), ptr(cf), ptr(c), ptr(w), stream_ptr()), "spuma_fv_weights")
+        return w
+
+    def fv_grad(self, sf, w, v, p, bface_cell=None, bface_sf=None, btype=None):
+        g = torch.empty((self.n_cells, 3), dtype=torch.float64, device=self.device)
+        nb = 0 if bface_cell is None else int(bface_cell.numel())
+        check(lib().spuma_fv_grad(self.handle, ptr(sf), ptr(w), ptr(v), nb, ptr(bface_cell), ptr(bface_sf),
+                                  ptr(btype), ptr(p), ptr(g), stream_ptr()), "spuma_fv_grad")
+        return g
+
+    def pressure_rhs(self, sf, c, w, gamma, grad, phi, bface_cell=None, bphi=None):
+        corr = torch.empty(self.n_faces, dtype=torch.float64, device=self.device)
+        b = torch.empty(self.n_cells, dtype=torch.float64, device=self.device)
+        nb = 0 if bface_cell is None else int(bface_cell.numel())
+        check(lib().spuma_pressure_rhs(self.handle, ptr(sf), ptr(c), ptr(w), ptr(gamma), ptr(grad), ptr(phi), nb,
+                                       ptr(bface_cell), ptr(bphi), ptr(corr), ptr(b), stream_ptr()),
+              "spuma_pressure_rhs")
+        return corr, b
+
+    def pressure_flux(self, upper, corr, p, phi, c, bface_cell=None, bface_sf=None, bface_cf=None, bgamma=None,
+                      btype=None, bphi=None):
+        out = torch.empty(self.n_faces, dtype=torch.float64, device=self.device)
+        nb = 0 if bface_cell is None else int(bface_cell.numel())
+        bout = torch.empty(nb, dtype=torch.float64, device=self.device)
+        check(lib().spuma_pressure_flux(self.handle, ptr(upper), ptr(corr), ptr(p), ptr(phi), nb, ptr(bface_cell),
+                                        ptr(bface_sf), ptr(bface_cf), ptr(bgamma), ptr(btype), ptr(c), ptr(bphi),
+                                        ptr(out), ptr(bout), stream_ptr()), "spuma_pressure_flux")
+        return out, bout
+
+    def fv_div(self, phi, bface_cell=None, bphi=None):
+        d = torch.empty(self.n_cells, dtype=torch.float64, device=self.device)
+        nb = 0 if bface_cell is None else int(bface_cell.numel())
+        check(lib().spuma_fv_div(self.handle, ptr(phi), nb, ptr(bface_cell), ptr(bphi), ptr(d), stream_ptr()),
+              "spuma_fv_div")
+        return d
+
+    def pressure_step(self, geom, gamma, bgamma, btype, phi, bphi, p_old, controls=None):
+        """One pressure correction (nNonOrthogonalCorrectors 0): assemble A,
+        b from div(phiHbyA) and the explicit correction with grad(p_old),
+        solve, reconstruct the flux.  geom = (sf, cf, c, v, bface_cell,
+        bface_sf, bface_cf).  Returns (p, phi, bphi, perf)."""
+        sf, cf, c, v, bcell, bsf, bcf = geom
+        upper, diag = self.assemble_laplacian(sf, c, gamma, bcell, bsf, bcf, bgamma, btype)
+        w = self.fv_weights(sf, cf, c)
+        g = self.fv_grad(sf, w, v, p_old, bcell, bsf, btype)
+        corr, b = self.pressure_rhs(sf, c, w, gamma, g, phi, bcell, bphi)
+        p, perf = self.solve(diag, upper, b, None, controls or SolverControls())
+        phin, bphin = self.pressure_flux(upper, corr, p, phi, c, bcell, bsf, bcf, bgamma, btype, bphi)
+        return p, phin, bphin, perf
+
     def amul(self, diag, upper, x, out=None):
         prec = F32 if x.dtype == torch.float32 else F64
         y = out if out is not None else torch.empty_like(x)

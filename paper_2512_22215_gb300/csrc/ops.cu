@@ -21,18 +21,6 @@ static int grid1d(int64_t work, int threads, int num_sms)
     return (int)std::max<int64_t>(g, 1);
 }
 
-// a = (gamma |S|) / max(n.d, 0.05 |d|), no contraction (bit-identical to the
-// sequential definition).
-__device__ __forceinline__ double face_coeff(double sx, double sy, double sz, double dx, double dy, double dz,
-                                             double gamma)
-{
-    const double mags = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)), __dmul_rn(sz, sz)));
-    const double magd = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
-    const double ndotd =
-        __ddiv_rn(__dadd_rn(__dadd_rn(__dmul_rn(sx, dx), __dmul_rn(sy, dy)), __dmul_rn(sz, dz)), mags);
-    const double denom = fmax(ndotd, __dmul_rn(0.05, magd));
-    return __ddiv_rn(__dmul_rn(gamma, mags), denom);
-}
 
 __global__ void k_face_coeff(int nf, const int* __restrict__ l, const int* __restrict__ u,
                              const double* __restrict__ sf, const double* __restrict__ c,
