@@ -58,6 +58,15 @@ def _declare(L):
     L.oracle_assembly_adjoint.argtypes = [_i32, _i32p, _i32p, _f64p, _f64p, _i32, _i32p, _f64p, _f64p, _i8p,
                                           _f64p, _f64p, _f64p, _f64p]
     L.oracle_assembly_adjoint.restype = None
+    L.oracle_amul_asym.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p]
+    L.oracle_amul_asym.restype = None
+    L.oracle_dilu_factor.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
+    L.oracle_dilu_factor.restype = _i32
+    L.oracle_dilu_precondition.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p]
+    L.oracle_dilu_precondition.restype = None
+    L.oracle_pbicg.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p, _i32, _f64, _f64,
+                               _i32, _i32, _f64p]
+    L.oracle_pbicg.restype = _i32
     L.oracle_fv_weights.argtypes = [_i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
     L.oracle_fv_weights.restype = None
     L.oracle_fv_grad.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _i32, _i32p, _f64p, _i8p, _f64p,
@@ -179,6 +188,43 @@ def fv_div(mesh, phi, bphi):
     lib().oracle_fv_div(mesh.n_cells, mesh.n_faces, _c(mesh.lower, np.int32), _c(mesh.upper_addr, np.int32),
                         _c(phi, np.float64), mesh.n_bfaces, _c(mesh.bface_cell, np.int32), _c(bphi, np.float64), d)
     return d
+
+
+# ------------------------------------------- asymmetric matrices: PBiCG ----
+def amul_asym(l, u, diag, lower, upper, x):
+    """y = A x with A_{u,l} = lower_f, A_{l,u} = upper_f (Tmul: swap lower/upper)."""
+    y = np.empty(len(diag))
+    lib().oracle_amul_asym(len(diag), len(l), _c(l, np.int32), _c(u, np.int32), _c(diag, np.float64),
+                           _c(lower, np.float64), _c(upper, np.float64), _c(x, np.float64), y)
+    return y
+
+
+def dilu_factor(l, u, diag, lower, upper):
+    """Returns (rD, first_bad_cell or -1)."""
+    rD = np.empty(len(diag))
+    bad = lib().oracle_dilu_factor(len(diag), len(l), _c(l, np.int32), _c(u, np.int32), _c(diag, np.float64),
+                                   _c(lower, np.float64), _c(upper, np.float64), rD)
+    return rD, bad
+
+
+def dilu_precondition(l, u, lower, upper, rD, r, transpose=False):
+    """w = M^-1 r (or M^-T r) for M = (D + L) D^-1 (D + U)."""
+    w = np.empty(len(rD))
+    lo, up = (upper, lower) if transpose else (lower, upper)
+    lib().oracle_dilu_precondition(len(rD), len(l), _c(l, np.int32), _c(u, np.int32), _c(lo, np.float64),
+                                   _c(up, np.float64), _c(rD, np.float64), _c(r, np.float64), w)
+    return w
+
+
+def pbicg(l, u, diag, lower, upper, b, x0=None, precond=3, tol=1e-8, rel_tol=0.0, max_iter=20000, min_iter=0):
+    """(x, perf) of OpenFOAM PBiCG; precond 0 none, 1 diagonal, 3 DILU."""
+    x = np.zeros(len(diag)) if x0 is None else np.array(x0, dtype=np.float64)
+    perf = np.zeros(5)
+    st = lib().oracle_pbicg(len(diag), len(l), _c(l, np.int32), _c(u, np.int32), _c(diag, np.float64),
+                            _c(lower, np.float64), _c(upper, np.float64), _c(b, np.float64), x, int(precond),
+                            float(tol), float(rel_tol), int(max_iter), int(min_iter), perf)
+    return x, dict(status=st, initial_residual=perf[0], final_residual=perf[1], n_iter=int(perf[2]),
+                   singular=int(perf[3]), converged=int(perf[4]))
 
 
 def amul(l, u, diag, upper, x):

@@ -665,3 +665,152 @@ void oracle_fv_div(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, co
     }
     for (int32_t b = 0; b < n_b; b++) div[bcell[b]] += bphi[b];
 }
+
+/* ======================================================================== */
+/* Asymmetric LDU matrices and PBiCG with DILU (the paper's momentum / k /  */
+/* omega solver: "PBiCG, preconditioner aDILU" in its fvSolution listing;  */
+/* "SpMVM (Amul + Tmul)" and "aDILUPreconditioner" in its profiling table,  */
+/* Sec. 4.2).  lduMatrix with lower != upper: A_{u(f),l(f)} = lower_f,      */
+/* A_{l(f),u(f)} = upper_f.                                                 */
+/* ======================================================================== */
+
+/* Amul:  y_i = d_i x_i; faces ascending: y_u += lower_f x_l; y_l += upper_f x_u */
+/* Tmul (A^T x): the same with lower and upper exchanged.  Each += is one FMA.  */
+void oracle_amul_asym(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, const double* diag,
+                      const double* lower, const double* upper, const double* x, double* y)
+{
+    for (int32_t i = 0; i < n; i++) y[i] = diag[i] * x[i];
+    for (int32_t f = 0; f < nf; f++) {
+        y[u[f]] = fma(lower[f], x[l[f]], y[u[f]]);
+        y[l[f]] = fma(upper[f], x[u[f]], y[l[f]]);
+    }
+}
+
+/* DILU factor: pivots p_i = d_i; faces ascending: p_u -= (upper_f lower_f) / p_l;
+ * rD_i = 1/p_i.  It makes diag((D + L) D^-1 (D + U)) = diag(A) with D = diag(p).
+ * Returns -1, or the first cell whose pivot is zero or not finite.            */
+int32_t oracle_dilu_factor(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, const double* diag,
+                           const double* lower, const double* upper, double* rD)
+{
+    for (int32_t i = 0; i < n; i++) rD[i] = diag[i];
+    for (int32_t f = 0; f < nf; f++) rD[u[f]] -= (upper[f] * lower[f]) / rD[l[f]];
+    int32_t bad = -1;
+    for (int32_t i = 0; i < n; i++) {
+        if (!(rD[i] != 0.0 && isfinite(rD[i])) && bad < 0) bad = i;
+        rD[i] = 1.0 / rD[i];
+    }
+    return bad;
+}
+
+/* DILU apply, w = M^-1 r with M = (D + L) D^-1 (D + U):
+ *   w_i = rD_i r_i; forward f ascending: w_u -= (rD_u lower_f) w_l;
+ *   backward f descending: w_l -= (rD_l upper_f) w_u.
+ * transpose (w = M^-T r): lower and upper exchanged.  Each -= one FMA of the
+ * rounded product.                                                          */
+void oracle_dilu_precondition(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, const double* lower,
+                              const double* upper, const double* rD, const double* r, double* w)
+{
+    for (int32_t i = 0; i < n; i++) w[i] = rD[i] * r[i];
+    for (int32_t f = 0; f < nf; f++) {
+        double c = rD[u[f]] * lower[f];
+        w[u[f]] = fma(-c, w[l[f]], w[u[f]]);
+    }
+    for (int32_t f = nf - 1; f >= 0; f--) {
+        double c = rD[l[f]] * upper[f];
+        w[l[f]] = fma(-c, w[u[f]], w[l[f]]);
+    }
+}
+
+/* OpenFOAM PBiCG (bi-conjugate gradients on A x = b and A^T x~ = b, with
+ * the same normalised L1 residual as PCG; normFactor from the row sums of A):
+ *   rA = b - A x, rT = b - A^T x; res0 = sum|rA|/normFactor; then
+ *   do { wArA_old = wArA; wA = M^-1 rA; wT = M^-T rT; wArA = sum wA rT;
+ *        first: pA = wA, pT = wT; else beta = wArA/wArA_old,
+ *        pA = wA + beta pA, pT = wT + beta pT;
+ *        wA = A pA; wT = A^T pT; wApT = sum wA pT;
+ *        singular if |wApT|/normFactor < 1e-300;
+ *        alpha = wArA/wApT; x += alpha pA; rA -= alpha wA; rT -= alpha wT;
+ *        res = sum|rA|/normFactor }
+ *   while the PCG loop condition holds.
+ * precond: 0 none, 1 diagonal, 3 DILU.  perf as oracle_pcg.                  */
+int32_t oracle_pbicg(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, const double* diag,
+                     const double* lower, const double* upper, const double* b, double* x, int32_t precond,
+                     double tol, double rel_tol, int32_t max_iter, int32_t min_iter, double* perf)
+{
+    size_t bytes = sizeof(double) * (size_t)(n > 0 ? n : 1);
+    double *rA = malloc(bytes), *rT = malloc(bytes), *wA = malloc(bytes), *wT = malloc(bytes);
+    double *pA = malloc(bytes), *pT = malloc(bytes), *rD = malloc(bytes), *s = malloc(bytes);
+    int32_t status = 0;
+    memset(perf, 0, 5 * sizeof(double));
+    oracle_amul_asym(n, nf, l, u, diag, lower, upper, x, wA);
+    oracle_amul_asym(n, nf, l, u, diag, upper, lower, x, wT);
+    for (int32_t i = 0; i < n; i++) {
+        rA[i] = b[i] - wA[i];
+        rT[i] = b[i] - wT[i];
+    }
+    /* normFactor: s = row sums of A, xbar = mean(x) */
+    for (int32_t i = 0; i < n; i++) s[i] = diag[i];
+    for (int32_t f = 0; f < nf; f++) {
+        s[u[f]] += lower[f];
+        s[l[f]] += upper[f];
+    }
+    double xbar = 0.0;
+    for (int32_t i = 0; i < n; i++) xbar += x[i];
+    xbar = n > 0 ? xbar / (double)n : 0.0;
+    double nfac = 0.0;
+    for (int32_t i = 0; i < n; i++) {
+        double t = s[i] * xbar;
+        nfac += fabs(wA[i] - t) + fabs(b[i] - t);
+    }
+    nfac += 1e-20;
+    double res0 = sum_mag(n, rA) / nfac, res = res0;
+    int32_t it = 0, singular = 0;
+    if (precond == 3) {
+        if (oracle_dilu_factor(n, nf, l, u, diag, lower, upper, rD) >= 0) { status = -2; goto done; }
+    } else if (precond == 1) {
+        oracle_diag_reciprocal(n, diag, rD);
+    }
+    if (min_iter > 0 || !converged(res0, res0, tol, rel_tol)) {
+        double wArA = 1.0, wArA_old;
+        do {
+            wArA_old = wArA;
+            if (precond == 3) {
+                oracle_dilu_precondition(n, nf, l, u, lower, upper, rD, rA, wA);
+                oracle_dilu_precondition(n, nf, l, u, upper, lower, rD, rT, wT);
+            } else if (precond == 1) {
+                for (int32_t i = 0; i < n; i++) { wA[i] = rD[i] * rA[i]; wT[i] = rD[i] * rT[i]; }
+            } else {
+                for (int32_t i = 0; i < n; i++) { wA[i] = rA[i]; wT[i] = rT[i]; }
+            }
+            wArA = sum_prod(n, wA, rT);
+            if (it == 0) {
+                for (int32_t i = 0; i < n; i++) { pA[i] = wA[i]; pT[i] = wT[i]; }
+            } else {
+                double beta = wArA / wArA_old;
+                for (int32_t i = 0; i < n; i++) {
+                    pA[i] = wA[i] + beta * pA[i];
+                    pT[i] = wT[i] + beta * pT[i];
+                }
+            }
+            oracle_amul_asym(n, nf, l, u, diag, lower, upper, pA, wA);
+            oracle_amul_asym(n, nf, l, u, diag, upper, lower, pT, wT);
+            double wApT = sum_prod(n, wA, pT);
+            if (fabs(wApT) / nfac < 1e-300) { singular = 1; break; }
+            double alpha = wArA / wApT;
+            for (int32_t i = 0; i < n; i++) {
+                x[i] += alpha * pA[i];
+                rA[i] -= alpha * wA[i];
+                rT[i] -= alpha * wT[i];
+            }
+            res = sum_mag(n, rA) / nfac;
+        } while ((++it < max_iter && !converged(res, res0, tol, rel_tol)) || it < min_iter);
+    }
+done:
+    perf[0] = res0;
+    perf[1] = res;
+    perf[2] = (double)it;
+    perf[3] = (double)singular;
+    perf[4] = (double)converged(res, res0, tol, rel_tol);
+    free(rA); free(rT); free(wA); free(wT); free(pA); free(pT); free(rD); free(s);
+    return status;
+}
