@@ -55,7 +55,15 @@ typedef enum {
 } spuma_status;
 
 typedef enum { SPUMA_F64 = 0, SPUMA_MIXED = 1, SPUMA_F32 = 2, SPUMA_MIXED_RESTART = 3 } spuma_precision;
-typedef enum { SPUMA_PRECOND_NONE = 0, SPUMA_PRECOND_DIAGONAL = 1, SPUMA_PRECOND_DIC = 2 } spuma_precond;
+typedef enum {
+    SPUMA_PRECOND_NONE = 0,
+    SPUMA_PRECOND_DIAGONAL = 1,
+    SPUMA_PRECOND_DIC = 2,
+    SPUMA_PRECOND_DILU = 3 /* asymmetric matrices, spuma_pbicg_solve only */
+} spuma_precond;
+
+/* spuma_workspace_bytes() flags */
+#define SPUMA_WORKSPACE_ASYMMETRIC 1 /* room for spuma_pbicg_solve (asymmetric matrices) */
 
 /* Solver controls, after OpenFOAM's fvSolution entries (paper appendix,
  * fvSolution listing: solver PCG, preconditioner, tolerance, relTol, maxIter,
@@ -107,7 +115,9 @@ typedef struct {
  * faces are sorted by (l, u) without duplicates.  The handle keeps pointers
  * into the workspace, which must stay allocated and untouched until
  * spuma_ldu_destroy().  The addressing arrays are copied; the caller may free
- * them after create returns.  flags: reserved, pass 0.
+ * them after create returns.  flags: 0, or SPUMA_WORKSPACE_ASYMMETRIC for a
+ * workspace that also holds what spuma_pbicg_solve needs (32F + 8N more
+ * bytes); create detects the larger size by itself.
  * ---------------------------------------------------------------------- */
 size_t spuma_workspace_bytes(int32_t n_cells, int32_t n_faces, int32_t flags);
 spuma_status spuma_ldu_create(int32_t n_cells, int32_t n_faces, const int32_t* lower_addr,
@@ -310,6 +320,30 @@ spuma_status spuma_pressure_flux(spuma_ldu_t h, const double* upper, const doubl
                                  double* phi_out, double* bphi_out, spuma_stream_t stream);
 spuma_status spuma_fv_div(spuma_ldu_t h, const double* phi, int32_t n_bfaces, const int32_t* bface_cell,
                           const double* bphi, double* div, spuma_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * PBiCG on an asymmetric LDU matrix (the paper's solver for U, k and omega:
+ * "PBiCG, preconditioner aDILU" in its fvSolution listing; "SpMVM (Amul +
+ * Tmul)" and "aDILUPreconditioner" in its profiling table, Sec. 4.2).
+ * A_{u(f),l(f)} = lower_f, A_{l(f),u(f)} = upper_f (OpenFOAM lduMatrix).
+ * OpenFOAM's bi-conjugate gradients: rA = b - A x, rT = b - A^T x; each
+ * iteration wA = M^-1 rA, wT = M^-T rT, wArA = wA.rT, pA = wA + beta pA,
+ * pT = wT + beta pT (beta = wArA/wArA_old), wA = A pA, wT = A^T pT,
+ * alpha = wArA/(wA.pT), x += alpha pA, rA -= alpha wA, rT -= alpha wT;
+ * residual, normFactor (row sums of A), singular test and stopping rule as
+ * spuma_pcg_solve.  Preconditioners: NONE, DIAGONAL, or DILU (M = (D + L)
+ * D^-1 (D + U), pivots d_u -= upper_f lower_f / d_l in face order, applied
+ * with the level-scheduled sweeps of the DIC path, one level per grid
+ * barrier; M^-T with lower and upper exchanged).  FP64 only (precision must
+ * be SPUMA_F64).  One persistent cooperative launch; x in/out (initial
+ * guess), perf as spuma_pcg_solve.  The workspace must have been sized with
+ * SPUMA_WORKSPACE_ASYMMETRIC, else SPUMA_ERR_WORKSPACE_TOO_SMALL; a zero or
+ * non-finite DILU pivot is reported as SPUMA_ERR_SINGULAR in perf.status.
+ * Invalidates a spuma_matrix_prepare()'d symmetric matrix.
+ * ---------------------------------------------------------------------- */
+spuma_status spuma_pbicg_solve(spuma_ldu_t h, const double* diag, const double* lower, const double* upper,
+                               const double* b, double* x, const spuma_solver_controls* ctl,
+                               spuma_solver_perf* perf, spuma_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Adjoint of x = A^-1 b for a loss L(x), given x and dldx = dL/dx:

@@ -17,7 +17,8 @@ SPUMA_OK = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_UPPER_TRIANGULAR", 3: "CUDA", 4: "WORKSPACE_TOO_SMALL",
                 5: "SINGULAR", 6: "NOT_SPD", 7: "NONFINITE", 8: "DEVICE_TIMEOUT"}
 F64, MIXED, F32, MIXED_RESTART = 0, 1, 2, 3
-PRECOND_NONE, PRECOND_DIAGONAL, PRECOND_DIC = 0, 1, 2
+PRECOND_NONE, PRECOND_DIAGONAL, PRECOND_DIC, PRECOND_DILU = 0, 1, 2, 3
+WORKSPACE_ASYMMETRIC = 1
 
 
 class Controls(C.Structure):
@@ -70,6 +71,7 @@ _SIGS = {
     "spuma_pcg_solve": (_I, [_H, _P, _P, _P, _P, C.POINTER(Controls), _P, _P]),
     "spuma_static_workspace_bytes": (C.c_size_t, []),
     "spuma_pcg_solve_static": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, C.POINTER(Controls), _P, _P]),
+    "spuma_pbicg_solve": (_I, [_H, _P, _P, _P, _P, _P, C.POINTER(Controls), _P, _P]),
     "spuma_pcg_adjoint": (_I, [_H, _P, _P, _P, _P, _P, _P, _P, C.POINTER(Controls), _P, _P]),
     "spuma_batch_create": (_I, [_I, C.POINTER(_H), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                 C.POINTER(Controls), _P, _I, _P, C.POINTER(_H)]),

@@ -7,8 +7,8 @@ from dataclasses import dataclass
 
 import torch
 
-from ._lib import (F32, F64, MIXED, PERF_BYTES, PRECOND_DIC, Controls, Perf, SpumaError, check, lib, ptr,
-                   stream_ptr)
+from ._lib import (F32, F64, MIXED, PERF_BYTES, PRECOND_DIC, PRECOND_DILU, WORKSPACE_ASYMMETRIC, Controls, Perf,
+                   SpumaError, check, lib, ptr, stream_ptr)
 
 
 @dataclass
@@ -44,7 +44,7 @@ def read_perf(t: torch.Tensor) -> list[dict]:
 class LduMesh:
     """A mesh's LDU addressing on the device plus the library workspace."""
 
-    def __init__(self, lower, upper_addr, n_cells: int, device="cuda", centres=None):
+    def __init__(self, lower, upper_addr, n_cells: int, device="cuda", centres=None, asymmetric=False):
         L = lib()
         dev = torch.device(device)
         lower = torch.as_tensor(lower, dtype=torch.int32).to(dev).contiguous()
@@ -52,7 +52,7 @@ class LduMesh:
         self.n_cells = int(n_cells)
         self.n_faces = int(lower.numel())
         self.device = dev
-        nbytes = L.spuma_workspace_bytes(self.n_cells, self.n_faces, 0)
+        nbytes = L.spuma_workspace_bytes(self.n_cells, self.n_faces, WORKSPACE_ASYMMETRIC if asymmetric else 0)
         # 256-byte alignment: the caching allocator returns 512-byte aligned blocks
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
         base = self.workspace.data_ptr()
@@ -214,6 +214,25 @@ class LduMesh:
         p = read_perf(perf)[0]
         if check_status and p["status"] != 0:
             raise SpumaError(p["status"], "device-side status of spuma_pcg_solve")
+        return x, p
+
+    def pbicg_solve(self, diag, lower, upper, b, x=None, controls: SolverControls | None = None, perf=None,
+                    check_status=True):
+        """PBiCG on the asymmetric A (A_{u,l} = lower_f, A_{l,u} = upper_f), in place of x
+        (x0 = 0 when x is None); the mesh must be created with asymmetric=True."""
+        ctl = (controls or SolverControls(precond=PRECOND_DILU)).c()
+        if x is None:
+            x = torch.zeros_like(b)
+        own_perf = perf is None
+        if own_perf:
+            perf = perf_tensor(1, self.device)
+        check(lib().spuma_pbicg_solve(self.handle, ptr(diag), ptr(lower), ptr(upper), ptr(b), ptr(x), C.byref(ctl),
+                                      ptr(perf), stream_ptr()), "spuma_pbicg_solve")
+        if not own_perf:
+            return x, perf
+        p = read_perf(perf)[0]
+        if check_status and p["status"] != 0:
+            raise SpumaError(p["status"], "device-side status of spuma_pbicg_solve")
         return x, p
 
     def adjoint(self, diag, upper, x, dldx, controls: SolverControls | None = None, want_diag=True,

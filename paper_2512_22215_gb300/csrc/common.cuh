@@ -269,9 +269,14 @@ struct Layout {
     size_t x32, r32, w32, p32, q32;
     // control
     size_t partials, bar, status, args, clk;
+    // asymmetric matrices (PBiCG), present when the workspace was sized with
+    // SPUMA_WORKSPACE_ASYMMETRIC: A^T's coefficients in the internal CSR, the
+    // transposed DILU sweep coefficients, the transposed search direction
+    size_t LaT64, UaT64, LcT64, UcT64, pT64;
+    bool asym = false;
 };
 
-Layout make_layout(int64_t n, int64_t nf);
+Layout make_layout(int64_t n, int64_t nf, bool asym = false);
 
 }  // namespace spuma
 

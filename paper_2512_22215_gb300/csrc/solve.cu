@@ -391,6 +391,27 @@ __device__ bool phase_gather(const SolveArgs& a, const Group& g)
 {
     RowIter it = rows_of(g);
     bool bad = false;
+    if (a.lower_orig) {
+        // asymmetric: row u's lower entry of face f holds lower_f (A) and
+        // upper_f (A^T), row l's upper entry upper_f (A) and lower_f (A^T)
+        for (int e = it.first; e < a.nf; e += it.stride) {
+            const int fl = a.Lface[e], fu = a.Uface[e];
+            const double lo = a.lower_orig[fl], lt = a.upper_orig[fl];
+            const double up = a.upper_orig[fu], ut = a.lower_orig[fu];
+            a.La64[e] = lo;
+            a.LaT64[e] = lt;
+            a.Ua64[e] = up;
+            a.UaT64[e] = ut;
+            bad |= !isfinite(lo) || !isfinite(lt);
+        }
+        for (int p = it.first; p < a.n; p += it.stride) {
+            const double dv = a.diag_orig[a.perm[p]];
+            a.d64[p] = dv;
+            bad |= !isfinite(dv);
+        }
+        if (bad) flag_error(a.status, SPUMA_ERR_NONFINITE, -1);
+        return group_sync(g);
+    }
     for (int e = it.first; e < a.nf; e += it.stride) {
         double lv = a.upper_orig[a.Lface[e]];
         double uv = a.upper_orig[a.Uface[e]];
@@ -425,6 +446,33 @@ __device__ bool phase_gather(const SolveArgs& a, const Group& g)
 __device__ bool phase_factor(const SolveArgs& a, const Group& g)
 {
     RowIter it = rows_of(g);
+    if (a.precond == SPUMA_PRECOND_DILU) {
+        // DILU pivots, level by level: p_u -= (upper_f lower_f) / p_l in face order
+        for (int L = 0; L < a.nlev; L++) {
+            const int r0 = a.lvl[L], r1 = a.lvl[L + 1];
+            for (int p = r0 + it.first; p < r1; p += it.stride) {
+                double piv = a.d64[p];
+                for (int e = a.Lptr[p]; e < a.Lptr[p + 1]; e++)
+                    piv = __dsub_rn(piv, __ddiv_rn(__dmul_rn(a.LaT64[e], a.La64[e]), a.rD64[a.Lcol[e]]));
+                a.rD64[p] = piv;
+                if (!(piv != 0.0 && isfinite(piv))) flag_error(a.status, SPUMA_ERR_SINGULAR, a.perm[p]);
+            }
+            if (!group_sync(g)) return false;
+        }
+        for (int p = it.first; p < a.n; p += it.stride) {
+            const double rd = __ddiv_rn(1.0, a.rD64[p]);
+            a.rD64[p] = rd;
+            for (int e = a.Lptr[p]; e < a.Lptr[p + 1]; e++) {
+                a.Lc64[e] = __dmul_rn(rd, a.La64[e]);
+                a.LcT64[e] = __dmul_rn(rd, a.LaT64[e]);
+            }
+            for (int e = a.Uptr[p]; e < a.Uptr[p + 1]; e++) {
+                a.Uc64[e] = __dmul_rn(rd, a.Ua64[e]);
+                a.UcT64[e] = __dmul_rn(rd, a.UaT64[e]);
+            }
+        }
+        return group_sync(g);
+    }
     if (a.precond == SPUMA_PRECOND_DIC) {
         for (int L = 0; L < a.nlev; L++) {
             const int r0 = a.lvl[L], r1 = a.lvl[L + 1];
@@ -470,10 +518,10 @@ __device__ bool phase_factor(const SolveArgs& a, const Group& g)
 // ------------------------------------------------------ DIC sweeps ---------
 // Forward rows of one level: w = rD r - sum (rD a) w_lower (ascending face
 // order); with `rho` (top level: no upper neighbours, so w is final here)
-// also rho += w r.
+// also rho += w dotv.
 template <class T>
 __device__ __forceinline__ void fwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int r1, int first, int stride, bool rho,
-                                         Acc<T>& arho)
+                                         const T* dotv, Acc<T>& arho)
 {
     constexpr int R = ChainShape<T>::R, G = ChainShape<T>::G;
     for (int pb = r0 + first; pb < r1; pb += R * stride) {
@@ -493,16 +541,16 @@ __device__ __forceinline__ void fwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int
         for (int k = 0; k < R; k++)
             if (p[k] < r1) {
                 v.w[p[k]] = ww[k];
-                if (rho) arho.prod(ww[k], rr[k]);
+                if (rho) arho.prod(ww[k], dotv == v.r ? rr[k] : dotv[p[k]]);
             }
     }
 }
 
 // Backward rows of one level: w -= sum (rD a) w_upper (descending face
-// order); rho += w r.
+// order); rho += w dotv (dotv may be NULL).
 template <class T>
 __device__ __forceinline__ void bwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int r1, int first, int stride,
-                                         Acc<T>& arho)
+                                         const T* dotv, Acc<T>& arho)
 {
     constexpr int R = ChainShape<T>::R, G = ChainShape<T>::G;
     for (int pb = r0 + first; pb < r1; pb += R * stride) {
@@ -521,46 +569,49 @@ __device__ __forceinline__ void bwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int
         for (int k = 0; k < R; k++)
             if (p[k] < r1) {
                 v.w[p[k]] = ww[k];
-                arho.prod(ww[k], v.r[p[k]]);
+                if (dotv) arho.prod(ww[k], dotv[p[k]]);
             }
     }
 }
 
-// w = M^-1 r with the DIC factor, and the block partials of rho = w.r in
-// slot B before the last grid barrier.  Forward sweep over levels 0 ..
+// w = M^-1 r with the DIC (or DILU) factor held in A's sweep coefficients,
+// and the block partials of rho = w.dotv (dotv = r by default) in `slot`
+// before the last grid barrier (slot < 0: no rho).  Forward sweep over levels 0 ..
 // nlev-1, backward over nlev-2 .. 0 (the top level has no upper neighbours:
 // its backward step would leave w as it is, so its rho terms are taken in the
 // forward step), one grid barrier per level.  The small last levels
 // (level >= tail_from) run on the group's first block alone, forward then
 // backward, with block-level barriers and one grid barrier after them.
 template <class T>
-__device__ bool dic_apply(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const Group& g, PhaseClock& pc)
+__device__ bool dic_apply(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const Group& g, PhaseClock& pc,
+                          const T* dotv = nullptr, int slot = SL_B)
 {
     const RowIter it = rows_of(g);
     const int nlev = a.nlev, tail = min(a.tail_from, nlev);
     const int tid = (int)threadIdx.x, bs = (int)blockDim.x;
+    if (!dotv && slot >= 0) dotv = v.r;
     Acc<T> arho;
     auto end_step = [&](bool last) {
-        if (last) {
+        if (last && slot >= 0) {
             double t[1] = {arho.value()};
-            block_reduce_store<1>(t, a.partials, SL_B, g.bid);
+            block_reduce_store<1>(t, a.partials, slot, g.bid);
         }
         return group_sync(g);
     };
     if (nlev == 0) return end_step(true);
     for (int L = 0; L < tail; L++) {
-        fwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], it.first, it.stride, L == nlev - 1, arho);
+        fwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], it.first, it.stride, L == nlev - 1 && dotv, dotv, arho);
         if (!end_step(nlev == 1)) return false;
         pc.lap(CK_FWD + min(L, 63));
     }
     if (tail < nlev) {
         if (g.bid == 0) {
             for (int L = tail; L < nlev; L++) {
-                fwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], tid, bs, L == nlev - 1, arho);
+                fwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], tid, bs, L == nlev - 1 && dotv, dotv, arho);
                 __syncthreads();
             }
             for (int L = nlev - 2; L >= tail; L--) {
-                bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], tid, bs, arho);
+                bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], tid, bs, dotv, arho);
                 __syncthreads();
             }
         }
@@ -568,7 +619,7 @@ __device__ bool dic_apply(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const 
         pc.lap(CK_FWD + min(tail, 63));
     }
     for (int L = min(tail, nlev - 1) - 1; L >= 0; L--) {
-        bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], it.first, it.stride, arho);
+        bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], it.first, it.stride, dotv, arho);
         if (!end_step(L == 0)) return false;
         pc.lap(CK_BWD + min(L, 63));
     }
@@ -970,7 +1021,105 @@ __device__ bool solve_mixed_restart(const SolveArgs& a, const Group& g, double n
 
 // Kinds of persistent launch, one kernel each so that every kernel holds only
 // its own path (register allocation is per kernel).
-enum SolveKind { KIND_SETUP = 0, KIND_F64 = 1, KIND_MIXED = 2, KIND_MIXED_RESTART = 3 };
+// -------------------------------------------------------------- PBiCG ---
+// OpenFOAM PBiCG on an asymmetric matrix (the paper's momentum solver: PBiCG
+// with DILU), FP64, after phase_init (x, rA = b - A x, normFactor from the
+// row sums of A).  Vectors: x, rA = r, wA = w, pA = p, wT = q, rT = b (the
+// right-hand side is not needed past rT = b - A^T x), pT.  A^T shares A's
+// structure: its lower entries of row u hold upper_f and its upper entries of
+// row l lower_f; the transposed DILU sweeps use rD times those.
+__device__ bool solve_pbicg(const SolveArgs& a, const Group& g, double nfac, double res0, spuma_solver_perf& pf)
+{
+    RowIter it = rows_of(g);
+    const Mat<double> A = mat_of<double>(a);
+    Mat<double> AT = A;
+    AT.La = a.LaT64;
+    AT.Ua = a.UaT64;
+    AT.Lc = a.LcT64;
+    AT.Uc = a.UcT64;
+    double *x = a.x, *rA = a.r, *wA = a.w, *pA = a.p, *wT = a.q, *rT = a.b, *pT = a.pT;
+    PhaseClock pc(a.phase_clk, g.bid);
+    for (int p = it.first; p < a.n; p += it.stride) rT[p] = a.b[p] - amul_row<double>(AT, x, p);
+    if (!group_sync(g)) return false;
+    double res = res0;
+    int n_it = 0, singular = 0;
+    if (a.min_iter > 0 || !converged(res0, res0, a.tol, a.rel_tol)) {
+        double wArA = 1.0, wArA_old, alpha = 0.0;
+        bool pending = false;
+        for (;;) {
+            if (pending) {
+                double acc[1] = {0.0};
+                for (int p = it.first; p < a.n; p += it.stride) {
+                    x[p] = fmadd(alpha, pA[p], x[p]);
+                    rA[p] = fmadd(-alpha, wA[p], rA[p]);
+                    rT[p] = fmadd(-alpha, wT[p], rT[p]);
+                    acc[0] += fabs(rA[p]);
+                }
+                block_reduce_store<1>(acc, a.partials, SL_D, g.bid);
+                if (!group_sync(g)) return false;
+                grid_reduce_read<1>(acc, a.partials, SL_D, g.nblocks);
+                res = acc[0] / nfac;
+                n_it++;
+                pc.lap(CK_UPD);
+                if (!((n_it < a.max_iter && !converged(res, res0, a.tol, a.rel_tol)) || n_it < a.min_iter)) break;
+            }
+            wArA_old = wArA;
+            if (a.precond == SPUMA_PRECOND_DILU) {
+                if (!dic_apply<double>(a, A, Vecs<double>{x, rA, wA, pA, wT}, g, pc, rT, SL_B)) return false;
+                if (!dic_apply<double>(a, AT, Vecs<double>{x, rT, wT, pT, wA}, g, pc, nullptr, -1)) return false;
+            } else {
+                double acc[1] = {0.0};
+                for (int p = it.first; p < a.n; p += it.stride) {
+                    const double wa = __dmul_rn(a.rD64[p], rA[p]);
+                    wA[p] = wa;
+                    wT[p] = __dmul_rn(a.rD64[p], rT[p]);
+                    acc[0] = fmadd(wa, rT[p], acc[0]);
+                }
+                block_reduce_store<1>(acc, a.partials, SL_B, g.bid);
+                if (!group_sync(g)) return false;
+                pc.lap(CK_DIAG);
+            }
+            double t[1];
+            grid_reduce_read<1>(t, a.partials, SL_B, g.nblocks);
+            wArA = t[0];
+            const bool first = !pending;
+            const double beta = first ? 0.0 : wArA / wArA_old;
+            for (int p = it.first; p < a.n; p += it.stride) {
+                pA[p] = first ? wA[p] : fmadd(beta, pA[p], wA[p]);
+                pT[p] = first ? wT[p] : fmadd(beta, pT[p], wT[p]);
+            }
+            if (!group_sync(g)) return false;
+            pc.lap(CK_PUPD);
+            double acc[1] = {0.0};
+            for (int p = it.first; p < a.n; p += it.stride) {
+                const double y = amul_row<double>(A, pA, p);
+                wA[p] = y;
+                wT[p] = amul_row<double>(AT, pT, p);
+                acc[0] = fmadd(y, pT[p], acc[0]);
+            }
+            block_reduce_store<1>(acc, a.partials, SL_C, g.bid);
+            if (!group_sync(g)) return false;
+            grid_reduce_read<1>(acc, a.partials, SL_C, g.nblocks);
+            pc.lap(CK_AMUL);
+            pc.count(CK_ITERS);
+            const double wApT = acc[0];
+            if (fabs(wApT) / nfac < 1e-300) {
+                singular = 1;
+                break;
+            }
+            alpha = wArA / wApT;
+            pending = true;
+        }
+    }
+    pf.initial_residual = res0;
+    pf.final_residual = res;
+    pf.n_iter = n_it;
+    pf.converged = converged(res, res0, a.tol, a.rel_tol);
+    pf.singular = singular;
+    return true;
+}
+
+enum SolveKind { KIND_SETUP = 0, KIND_F64 = 1, KIND_MIXED = 2, KIND_MIXED_RESTART = 3, KIND_PBICG = 4 };
 
 template <int KIND>
 __device__ void run_system(const SolveArgs& a, const Group& g)
@@ -1014,7 +1163,9 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
             double nfac = 1.0, res0 = 0.0;
             ok = phase_init(a, g, &nfac, &res0);
             if (ok) {
-                if constexpr (KIND == KIND_MIXED) {
+                if constexpr (KIND == KIND_PBICG) {
+                    ok = solve_pbicg(a, g, nfac, res0, pf);
+                } else if constexpr (KIND == KIND_MIXED) {
                     ok = solve_mixed_reliable(a, g, nfac, res0, pf);
                 } else if constexpr (KIND == KIND_MIXED_RESTART) {
                     ok = solve_mixed_restart(a, g, nfac, pf);
@@ -1126,6 +1277,12 @@ SolveArgs make_args(spuma_ldu_t h)
     a.Uc64 = h->at<double>(L.Uc64);
     a.d64 = h->at<double>(L.d64);
     a.rD64 = h->at<double>(L.rD64);
+    a.lower_orig = nullptr;
+    a.LaT64 = L.asym ? h->at<double>(L.LaT64) : nullptr;
+    a.UaT64 = L.asym ? h->at<double>(L.UaT64) : nullptr;
+    a.LcT64 = L.asym ? h->at<double>(L.LcT64) : nullptr;
+    a.UcT64 = L.asym ? h->at<double>(L.UcT64) : nullptr;
+    a.pT = L.asym ? h->at<double>(L.pT64) : nullptr;
     a.Ecol = h->at<int>(L.Ecol);
     a.Ea64 = h->at<double>(L.Ea64);
     a.Ea32 = h->at<float>(L.Ea32);
@@ -1156,6 +1313,7 @@ SolveArgs make_args(spuma_ldu_t h)
 static int kind_of(const SolveArgs& a)
 {
     if (a.mode != MODE_SOLVE) return KIND_SETUP;
+    if (a.lower_orig) return KIND_PBICG;
     if (a.precision == SPUMA_MIXED) return KIND_MIXED;
     if (a.precision == SPUMA_MIXED_RESTART) return KIND_MIXED_RESTART;
     return KIND_F64;
@@ -1167,6 +1325,7 @@ static const void* solve_kernel(int kind)
     case KIND_SETUP: return (const void*)k_solve<KIND_SETUP>;
     case KIND_MIXED: return (const void*)k_solve<KIND_MIXED>;
     case KIND_MIXED_RESTART: return (const void*)k_solve<KIND_MIXED_RESTART>;
+    case KIND_PBICG: return (const void*)k_solve<KIND_PBICG>;
     default: return (const void*)k_solve<KIND_F64>;
     }
 }
@@ -1339,6 +1498,45 @@ spuma_status pcg_solve_internal(spuma_ldu_t h, const double* diag, const double*
 using namespace spuma;
 
 extern "C" {
+
+spuma_status spuma_pbicg_solve(spuma_ldu_t h, const double* diag, const double* lower, const double* upper,
+                               const double* b, double* x, const spuma_solver_controls* ctl, spuma_solver_perf* perf,
+                               spuma_stream_t stream)
+{
+    if (!h || !ctl || (ctl->precond != SPUMA_PRECOND_NONE && ctl->precond != SPUMA_PRECOND_DIAGONAL &&
+                       ctl->precond != SPUMA_PRECOND_DILU) ||
+        ctl->precision != SPUMA_F64 || !(ctl->tolerance >= 0.0) || !(ctl->rel_tol >= 0.0) || ctl->max_iter < 0 ||
+        ctl->min_iter < 0 || (h->n > 0 && (!diag || !b || !x)) || (h->nf > 0 && (!lower || !upper))) {
+        set_error("spuma_pbicg_solve: bad argument (precond NONE, DIAGONAL or DILU; precision F64)");
+        return SPUMA_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->n == 0) {
+        if (perf) {
+            spuma_solver_perf z{};
+            z.converged = 1;
+            SPUMA_CUDA(cudaMemcpyAsync(perf, &z, sizeof(z), cudaMemcpyHostToDevice, s));
+        }
+        return SPUMA_OK;
+    }
+    if (!h->L.asym) {
+        set_error("spuma_pbicg_solve: the workspace was not sized with SPUMA_WORKSPACE_ASYMMETRIC");
+        return SPUMA_ERR_WORKSPACE_TOO_SMALL;
+    }
+    SolveArgs a = make_args(h);
+    fill_controls(a, ctl);
+    a.mode = MODE_SOLVE;
+    a.zero_x0 = 0;
+    a.diag_orig = diag;
+    a.upper_orig = upper;
+    a.lower_orig = lower;
+    a.b_orig = b;
+    a.x_orig = x;
+    a.perf = perf;
+    a.ell_w = 0;   // the fixed-width layout holds no asymmetric coefficients: row-extent Amul/Tmul
+    h->prepared_precond = -1;
+    return launch_solve(h, a, default_threads(ctl), s);
+}
 
 spuma_status spuma_matrix_prepare(spuma_ldu_t h, const double* diag, const double* upper, int32_t precond,
                                   spuma_stream_t stream)

@@ -22,12 +22,14 @@ struct SolveArgs {
     // original-order inputs/outputs
     const double* diag_orig;
     const double* upper_orig;
+    const double* lower_orig;  // asymmetric matrix (PBiCG): lower coefficients; NULL when symmetric
     const double* b_orig;
     double* x_orig;
     // internal matrix
     const int *Lptr, *Lcol, *Lface, *Uptr, *Ucol, *Uface;
     double *La64, *Ua64, *Lc64, *Uc64, *d64, *rD64;
     float *La32, *Ua32, *Lc32, *Uc32, *d32, *rD32;
+    double *LaT64, *UaT64, *LcT64, *UcT64, *pT;  // asymmetric regions (NULL without them)
     const int* Ecol;       // fixed-width Amul layout (ell_w > 0): columns, entry j of row p at j n + p
     double* Ea64;
     float* Ea32;

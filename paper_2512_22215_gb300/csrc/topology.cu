@@ -29,7 +29,7 @@ uint64_t barrier_timeout_ns() { return g_timeout_ns.load(); }
 
 static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-Layout make_layout(int64_t n, int64_t nf)
+Layout make_layout(int64_t n, int64_t nf, bool asym)
 {
     Layout L;
     size_t off = 0;
@@ -89,6 +89,14 @@ Layout make_layout(int64_t n, int64_t nf)
     L.status = take(256);
     L.args = take(4096);
     L.clk = take(8 * 256);
+    if (asym) {
+        L.asym = true;
+        L.LaT64 = take(d8f);
+        L.UaT64 = take(d8f);
+        L.LcT64 = take(d8f);
+        L.UcT64 = take(d8f);
+        L.pT64 = take(d8n);
+    }
     L.bytes = off;
     return L;
 }
@@ -510,9 +518,8 @@ void spuma_set_barrier_timeout_ns(uint64_t ns) { g_timeout_ns = ns; }
 
 size_t spuma_workspace_bytes(int32_t n_cells, int32_t n_faces, int32_t flags)
 {
-    (void)flags;
     if (n_cells < 0 || n_faces < 0) return 0;
-    return make_layout(n_cells, n_faces).bytes;
+    return make_layout(n_cells, n_faces, (flags & SPUMA_WORKSPACE_ASYMMETRIC) != 0).bytes;
 }
 
 spuma_status spuma_ldu_create(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, void* workspace,
@@ -532,6 +539,11 @@ spuma_status spuma_ldu_create_with_centres(int32_t n, int32_t nf, const int32_t*
     if (!workspace) { set_error("workspace is NULL"); return SPUMA_ERR_INVALID_ARG; }
     if (((uintptr_t)workspace & 255u) != 0) { set_error("workspace must be 256-byte aligned"); return SPUMA_ERR_INVALID_ARG; }
     Layout L = make_layout(n, nf);
+    {
+        // the asymmetric regions follow the symmetric layout when they fit
+        const Layout La = make_layout(n, nf, true);
+        if (workspace_bytes >= La.bytes) L = La;
+    }
     if (workspace_bytes < L.bytes) {
         set_error("workspace needs " + std::to_string(L.bytes) + " bytes");
         return SPUMA_ERR_WORKSPACE_TOO_SMALL;
