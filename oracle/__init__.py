@@ -58,6 +58,10 @@ def _declare(L):
     L.oracle_assembly_adjoint.argtypes = [_i32, _i32p, _i32p, _f64p, _f64p, _i32, _i32p, _f64p, _f64p, _i8p,
                                           _f64p, _f64p, _f64p, _f64p]
     L.oracle_assembly_adjoint.restype = None
+    L.oracle_dot.argtypes = [_i32, _f64p, _f64p]
+    L.oracle_dot.restype = _f64
+    L.oracle_jacobi_sweep.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+    L.oracle_jacobi_sweep.restype = None
     L.oracle_amul_asym.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p]
     L.oracle_amul_asym.restype = None
     L.oracle_dilu_factor.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
@@ -225,6 +229,19 @@ def pbicg(l, u, diag, lower, upper, b, x0=None, precond=3, tol=1e-8, rel_tol=0.0
                             float(tol), float(rel_tol), int(max_iter), int(min_iter), perf)
     return x, dict(status=st, initial_residual=perf[0], final_residual=perf[1], n_iter=int(perf[2]),
                    singular=int(perf[3]), converged=int(perf[4]))
+
+
+def dot(a, b):
+    """sum a_i b_i in ascending order."""
+    return lib().oracle_dot(len(a), _c(a, np.float64), _c(b, np.float64))
+
+
+def jacobi_sweep(l, u, diag, upper, wrd, r, e):
+    """One damped-Jacobi sweep in place: e_i = fma(wrd_i, r_i - (A e)_i, e_i)."""
+    q = np.empty(len(diag))
+    lib().oracle_jacobi_sweep(len(diag), len(l), _c(l, np.int32), _c(u, np.int32), _c(diag, np.float64),
+                              _c(upper, np.float64), _c(wrd, np.float64), _c(r, np.float64), e, q)
+    return e
 
 
 def amul(l, u, diag, upper, x):

@@ -814,3 +814,16 @@ done:
     free(rA); free(rT); free(wA); free(wT); free(pA); free(pT); free(rD); free(s);
     return status;
 }
+
+/* One damped-Jacobi (Richardson) sweep of the GAMG smoother:               */
+/*   q = A e (oracle_amul), then e_i = fma(wrd_i, r_i - q_i, e_i), wrd_i =   */
+/*   omega rD_i.  q is scratch.                                              */
+void oracle_jacobi_sweep(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, const double* diag,
+                         const double* upper, const double* wrd, const double* r, double* e, double* q)
+{
+    oracle_amul(n, nf, l, u, diag, upper, e, q);
+    for (int32_t i = 0; i < n; i++) e[i] = fma(wrd[i], r[i] - q[i], e[i]);
+}
+
+/* sum_i a_i b_i in ascending order (GAMG correction scaling). */
+double oracle_dot(int32_t n, const double* a, const double* b) { return sum_prod(n, a, b); }
