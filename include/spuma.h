@@ -346,6 +346,44 @@ spuma_status spuma_pbicg_solve(spuma_ldu_t h, const double* diag, const double* 
                                spuma_solver_perf* perf, spuma_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * GAMG for the pressure equation (the paper's production pressure solver:
+ * "GAMG, smoother Richardson" in its fvSolution listing; Richardson (damped
+ * Jacobi) on every level and a diagonal PCG at the coarsest one, with
+ * OpenFOAM's coarsening unmodified, Sec. 4.3).
+ * spuma_gamg_create: builds the level hierarchy on the HOST (synchronous;
+ *   it copies the addressing and face_weight[F] (device, e.g. |S_f|) back):
+ *   pairwise agglomeration by face weight, cells in ascending order (pair
+ *   with the unassigned neighbour across the heaviest face, first in face
+ *   order on ties; join the aggregate across the heaviest face when all
+ *   neighbours are taken; no faces: stay alone); coarse faces between
+ *   different aggregates, sorted by (min, max), weights summed; levels added
+ *   while the coarse level has more than 10 cells and fewer than the level
+ *   above.  spuma_gamg_workspace_bytes then gives the device workspace that
+ *   spuma_gamg_bind takes (256-byte aligned; synchronous upload).
+ * spuma_gamg_solve: one persistent cooperative launch: Galerkin coarse
+ *   matrices P^T A P (P piecewise constant; sums in ascending fine order:
+ *   upper_F = sum of the fine upper_f of F; diag_C = sum of the fine diag of
+ *   C, then + 2 upper_f of each fine face inside C), then the iterations
+ *   x += V(0, r), r = b - A x with PCG's normalised residual, normFactor and
+ *   stopping rule (tolerance, rel_tol, max_iter, min_iter; precision F64).
+ *   V(k, r): no pre-smoothing; r_{k+1} = sum over each aggregate; at the
+ *   coarsest level diagonal PCG from 0 to 1e-8 relative; e_k = injection of
+ *   e_{k+1}, scaled by (e.r)/(e.A e) when e.A e > 0; two damped-Jacobi sweeps
+ *   e_i = fma(omega/d_i, r_i - (A e)_i, e_i), omega = 2/3.  x in/out (initial
+ *   guess), original order; perf as spuma_pcg_solve (n_levels = GAMG levels).
+ *   The hierarchy's handle h must outlive the GAMG object; its status and
+ *   barrier words are shared with h's other calls (stream-ordered).
+ * ---------------------------------------------------------------------- */
+typedef struct spuma_gamg* spuma_gamg_t;
+spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_stream_t stream, spuma_gamg_t* out);
+size_t spuma_gamg_workspace_bytes(spuma_gamg_t g);
+spuma_status spuma_gamg_bind(spuma_gamg_t g, void* workspace, size_t workspace_bytes, spuma_stream_t stream);
+spuma_status spuma_gamg_info(spuma_gamg_t g, int32_t* n_levels, int32_t* level_cells, int32_t max_levels);
+spuma_status spuma_gamg_solve(spuma_gamg_t g, const double* diag, const double* upper, const double* b, double* x,
+                              const spuma_solver_controls* ctl, spuma_solver_perf* perf, spuma_stream_t stream);
+spuma_status spuma_gamg_destroy(spuma_gamg_t g);
+
+/* ------------------------------------------------------------------------
  * Adjoint of x = A^-1 b for a loss L(x), given x and dldx = dL/dx:
  *   A lambda = dldx (A symmetric: A^T = A, same PCG, lambda from 0);
  *   dL/db = lambda;  dL/dupper_f = -(lambda_{l(f)} x_{u(f)} + lambda_{u(f)} x_{l(f)});

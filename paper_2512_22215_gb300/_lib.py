@@ -71,6 +71,12 @@ _SIGS = {
     "spuma_pcg_solve": (_I, [_H, _P, _P, _P, _P, C.POINTER(Controls), _P, _P]),
     "spuma_static_workspace_bytes": (C.c_size_t, []),
     "spuma_pcg_solve_static": (_I, [_I, _I, _P, _P, _P, _P, _P, _P, C.POINTER(Controls), _P, _P]),
+    "spuma_gamg_create": (_I, [_H, _P, _P, C.POINTER(_H)]),
+    "spuma_gamg_workspace_bytes": (C.c_size_t, [_H]),
+    "spuma_gamg_bind": (_I, [_H, _P, C.c_size_t, _P]),
+    "spuma_gamg_info": (_I, [_H, C.POINTER(_I), _P, _I]),
+    "spuma_gamg_solve": (_I, [_H, _P, _P, _P, _P, C.POINTER(Controls), _P, _P]),
+    "spuma_gamg_destroy": (_I, [_H]),
     "spuma_pbicg_solve": (_I, [_H, _P, _P, _P, _P, _P, C.POINTER(Controls), _P, _P]),
     "spuma_pcg_adjoint": (_I, [_H, _P, _P, _P, _P, _P, _P, _P, C.POINTER(Controls), _P, _P]),
     "spuma_batch_create": (_I, [_I, C.POINTER(_H), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libspuma.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["topology.cu", "solve.cu", "ops.cu", "fvops.cu", "batch.cu", "noalloc.cu"]
+SOURCES = ["topology.cu", "solve.cu", "ops.cu", "fvops.cu", "gamg.cu", "batch.cu", "noalloc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-Xptxas", "-v"]

@@ -250,6 +250,51 @@ class LduMesh:
         return dldb, dldu, dldd, p
 
 
+class GamgSolver:
+    """GAMG for a mesh's symmetric pressure matrices: the level hierarchy from
+    the face weights (e.g. |S_f|), built once, then any number of solves."""
+
+    def __init__(self, mesh: LduMesh, face_weight):
+        L = lib()
+        self.mesh = mesh
+        fw = torch.as_tensor(face_weight, dtype=torch.float64).to(mesh.device).contiguous()
+        h = C.c_void_p()
+        check(L.spuma_gamg_create(mesh.handle, ptr(fw), stream_ptr(), C.byref(h)), "spuma_gamg_create")
+        self.handle = h
+        nbytes = L.spuma_gamg_workspace_bytes(h)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=mesh.device)
+        base = (self.workspace.data_ptr() + 255) // 256 * 256
+        check(L.spuma_gamg_bind(h, base, nbytes, stream_ptr()), "spuma_gamg_bind")
+        nl = C.c_int32()
+        cells = (C.c_int32 * 64)()
+        check(L.spuma_gamg_info(h, C.byref(nl), C.cast(cells, C.c_void_p), 64), "spuma_gamg_info")
+        self.level_cells = [cells[k] for k in range(min(nl.value, 64))]
+
+    def solve(self, diag, upper, b, x=None, controls: SolverControls | None = None, perf=None, check_status=True):
+        ctl = (controls or SolverControls()).c()
+        if x is None:
+            x = torch.zeros_like(b)
+        own_perf = perf is None
+        if own_perf:
+            perf = perf_tensor(1, self.mesh.device)
+        check(lib().spuma_gamg_solve(self.handle, ptr(diag), ptr(upper), ptr(b), ptr(x), C.byref(ctl), ptr(perf),
+                                     stream_ptr()), "spuma_gamg_solve")
+        if not own_perf:
+            return x, perf
+        p = read_perf(perf)[0]
+        if check_status and p["status"] != 0:
+            raise SpumaError(p["status"], "device-side status of spuma_gamg_solve")
+        return x, p
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            try:
+                lib().spuma_gamg_destroy(h)
+            except Exception:
+                pass
+
+
 class BatchSolve:
     """Many systems in one persistent launch, replayed from a CUDA graph."""
 

@@ -1,0 +1,693 @@
+// gamg.cu -- GAMG for the pressure equation (the paper's production pressure
+// solver: "GAMG, smoother Richardson", Richardson on every level and a
+// diagonal-preconditioned PCG at the coarsest one, with OpenFOAM's coarsening
+// unmodified).
+//
+// The hierarchy depends on the mesh only (faces and their area weights), so
+// it is built once, on the host, when the solver object is created, as
+// OpenFOAM caches its agglomeration: pairwise agglomeration by face weight,
+// cells in ascending order; an unassigned cell pairs with its unassigned
+// neighbour across the heaviest face (first in face order on ties); a cell
+// whose neighbours are all taken joins the aggregate across its heaviest
+// face; a cell without faces stays alone.  The coarse graph keeps the faces
+// between different aggregates, (min, max) ordered and sorted, with summed
+// weights; levels are added while the coarse level has more than 10 cells
+// and fewer cells than the level above.
+//
+// Every solve runs in one persistent cooperative launch: the Galerkin
+// coarse matrices (P^T A P with piecewise-constant P, sums in ascending fine
+// order), then the outer iterations x += V(0, r), r = b - A x with PCG's
+// normalised residual and stopping rule.  V(k, r): no pre-smoothing;
+// restriction (sum over the aggregate); the coarsest level by diagonal PCG
+// from 0 to 1e-8 relative; prolongation by injection, scaled by the A-norm
+// optimal step (e.r)/(e.Ae); two damped-Jacobi sweeps e += (2/3 rD)(r - Ae).
+// Levels of at most two rows per thread of one block run on the first block
+// alone with block-level barriers; the others on the whole grid.  Every
+// per-row sum follows the sequential definition's order; dot products are
+// deterministic block/grid reductions.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace spuma {
+
+constexpr int kGamgMaxLevels = 50;
+constexpr int kGamgCoarsest = 10;
+constexpr double kGamgOmega = 2.0 / 3.0;
+constexpr int kGamgPostSweeps = 2;
+constexpr double kGamgCoarseRelTol = 1e-8;
+enum GamgSlot { GS_A = 0, GS_B = 1, GS_C = 2, GS_D = 3 };   // reduction slots
+
+// Device view of one level (rows in the original order of that level).
+struct GamgLevel {
+    int n, nf;
+    const int *rptr, *rcol, *rfac;          // row CSR for A_k: entries in ascending face order
+    const int* agg;                         // cell -> next-level cell (k < L-1)
+    const int *cptr, *ccell;                // next-level cell -> its cells (ascending)
+    const int *fptr, *fface;                // next-level face -> its faces (ascending)
+    const int *iptr, *iface;                // next-level cell -> the faces inside it (ascending)
+    const double *diag, *upper;             // A_k (level 0: the caller's arrays)
+    double *cdiag, *cupper;                 // A_{k+1} written here (k < L-1)
+    double *wrd;                            // omega / diag
+    double *r, *e, *q;                      // right-hand side, correction, scratch
+};
+
+struct GamgArgs {
+    int nlev, small_from;
+    const GamgLevel* lv;                    // device array [nlev]
+    const double* b_orig;
+    double* x_orig;
+    double *x, *b, *res;                    // level-0 solution, rhs, outer residual (= lv[0].r)
+    double *pw, *pp, *pq, *px;              // coarsest-level PCG vectors
+    double* partials;
+    int* status;
+    spuma_solver_perf* perf;
+    int max_iter, min_iter;
+    double tol, rel_tol;
+};
+
+// --------------------------------------------------------------- device ---
+struct Exec {
+    int first, stride;
+    bool grid, active;
+};
+
+__device__ __forceinline__ Exec exec_for(const GamgArgs& a, int k, const Group& g)
+{
+    if (k >= a.small_from)
+        return Exec{(int)threadIdx.x, (int)blockDim.x, false, g.bid == 0};
+    return Exec{g.bid * (int)blockDim.x + (int)threadIdx.x, g.nblocks * (int)blockDim.x, true, true};
+}
+
+// Barrier after a step done with `x`: the grid barrier, or the first block's
+// block barrier (the other blocks skip it).
+__device__ __forceinline__ bool exec_sync(const Exec& x, const Group& g)
+{
+    if (x.grid) return group_sync(g);
+    if (g.bid == 0) __syncthreads();
+    return true;
+}
+
+// Sums of NV values over the executing threads, returned to them.
+template <int NV>
+__device__ __forceinline__ bool exec_sum(const Exec& x, double (&v)[NV], const GamgArgs& a, int slot,
+                                         const Group& g)
+{
+    if (x.grid) {
+        block_reduce_store<NV>(v, a.partials, slot, g.bid);
+        if (!group_sync(g)) return false;
+        grid_reduce_read<NV>(v, a.partials, slot, g.nblocks);
+        return true;
+    }
+    if (g.bid != 0) return true;
+    block_reduce_store<NV>(v, a.partials, slot, 0);
+    __syncthreads();
+    grid_reduce_read<NV>(v, a.partials, slot, 1);
+    return true;
+}
+
+__device__ __forceinline__ double gamg_amul_row(const GamgLevel& L, const double* d, const double* up,
+                                                const double* x, int i)
+{
+    double y = __dmul_rn(d[i], x[i]);
+    for (int e = L.rptr[i]; e < L.rptr[i + 1]; e++) y = __fma_rn(up[L.rfac[e]], x[L.rcol[e]], y);
+    return y;
+}
+
+// Galerkin coarse matrices level by level, then omega/diag on every level.
+__device__ bool gamg_coarse_matrices(const GamgArgs& a, const Group& g)
+{
+    for (int k = 0; k + 1 < a.nlev; k++) {
+        const GamgLevel& F = a.lv[k];
+        const Exec x = exec_for(a, k + 1, g);
+        if (x.active) {
+            const int nfc = a.lv[k + 1].nf, nc = a.lv[k + 1].n;
+            for (int c = x.first; c < nfc; c += x.stride) {
+                double s = 0.0;
+                for (int j = F.fptr[c]; j < F.fptr[c + 1]; j++) s = __dadd_rn(s, F.upper[F.fface[j]]);
+                F.cupper[c] = s;
+            }
+            for (int c = x.first; c < nc; c += x.stride) {
+                double s = 0.0;
+                for (int j = F.cptr[c]; j < F.cptr[c + 1]; j++) s = __dadd_rn(s, F.diag[F.ccell[j]]);
+                for (int j = F.iptr[c]; j < F.iptr[c + 1]; j++) s = __dadd_rn(s, __dmul_rn(2.0, F.upper[F.iface[j]]));
+                F.cdiag[c] = s;
+            }
+        }
+        if (!exec_sync(x, g)) return false;
+    }
+    // the first block's levels become visible to every block here
+    if (!group_sync(g)) return false;
+    const int first = g.bid * (int)blockDim.x + (int)threadIdx.x, stride = g.nblocks * (int)blockDim.x;
+    for (int k = 0; k < a.nlev; k++) {
+        const GamgLevel& L = a.lv[k];
+        for (int i = first; i < L.n; i += stride) L.wrd[i] = __dmul_rn(kGamgOmega, __ddiv_rn(1.0, L.diag[i]));
+    }
+    return group_sync(g);
+}
+
+// Coarsest level: PCG with the diagonal preconditioner from 0, relative
+// tolerance kGamgCoarseRelTol, at most 2n + 10 iterations (PCG recurrences).
+__device__ bool gamg_coarsest(const GamgArgs& a, const Group& g)
+{
+    const int k = a.nlev - 1;
+    const GamgLevel& L = a.lv[k];
+    const Exec x = exec_for(a, k, g);
+    if (!x.active) return true;   // the coarsest level is the first block's alone
+    double* e = L.e;
+    double* r = a.pw;   // residual
+    double *w = a.pq, *p = a.pp, *q = a.px;
+    double v[1] = {0.0};
+    if (x.active)
+        for (int i = x.first; i < L.n; i += x.stride) {
+            e[i] = 0.0;
+            r[i] = L.r[i];
+            v[0] += fabs(L.r[i]);
+        }
+    if (!exec_sum<1>(x, v, a, GS_A, g)) return false;
+    const double nfac = v[0] + 1e-20;   // x = 0: sum|A x - 0| + sum|b - 0|
+    const double res0 = v[0] / nfac;
+    double res = res0, rho = 1.0, rho_old;
+    const int max_it = 2 * L.n + 10;
+    int it = 0;
+    if (res0 > 0.0) {
+        do {
+            rho_old = rho;
+            double t[1] = {0.0};
+            if (x.active)
+                for (int i = x.first; i < L.n; i += x.stride) {
+                    const double wi = __dmul_rn(__ddiv_rn(1.0, L.diag[i]), r[i]);
+                    w[i] = wi;
+                    t[0] = __fma_rn(wi, r[i], t[0]);
+                }
+            if (!exec_sum<1>(x, t, a, GS_B, g)) return false;
+            rho = t[0];
+            const double beta = it == 0 ? 0.0 : rho / rho_old;
+            if (x.active)
+                for (int i = x.first; i < L.n; i += x.stride) p[i] = it == 0 ? w[i] : __fma_rn(beta, p[i], w[i]);
+            if (!exec_sync(x, g)) return false;
+            double s[1] = {0.0};
+            if (x.active)
+                for (int i = x.first; i < L.n; i += x.stride) {
+                    const double qi = gamg_amul_row(L, L.diag, L.upper, p, i);
+                    q[i] = qi;
+                    s[0] = __fma_rn(qi, p[i], s[0]);
+                }
+            if (!exec_sum<1>(x, s, a, GS_C, g)) return false;
+            if (fabs(s[0]) / nfac < 1e-300) break;
+            const double alpha = rho / s[0];
+            double m[1] = {0.0};
+            if (x.active)
+                for (int i = x.first; i < L.n; i += x.stride) {
+                    e[i] = __fma_rn(alpha, p[i], e[i]);
+                    r[i] = __fma_rn(-alpha, q[i], r[i]);
+                    m[0] += fabs(r[i]);
+                }
+            if (!exec_sum<1>(x, m, a, GS_D, g)) return false;
+            res = m[0] / nfac;
+        } while (++it < max_it && !(res < kGamgCoarseRelTol * res0));
+    }
+    return exec_sync(x, g);
+}
+
+// e_0 = V(0, r_0), with r_0 = a.res.
+__device__ bool gamg_vcycle(const GamgArgs& a, const Group& g)
+{
+    // restriction down to the coarsest level
+    for (int k = 0; k + 1 < a.nlev; k++) {
+        const GamgLevel& F = a.lv[k];
+        const GamgLevel& C = a.lv[k + 1];
+        const Exec x = exec_for(a, k + 1, g);
+        if (x.active)
+            for (int c = x.first; c < C.n; c += x.stride) {
+                double s = 0.0;
+                for (int j = F.cptr[c]; j < F.cptr[c + 1]; j++) s = __dadd_rn(s, F.r[F.ccell[j]]);
+                C.r[c] = s;
+            }
+        if (!exec_sync(x, g)) return false;
+    }
+    if (!gamg_coarsest(a, g)) return false;
+    // prolongation, scaling and smoothing back up
+    for (int k = a.nlev - 2; k >= 0; k--) {
+        const GamgLevel& L = a.lv[k];
+        const GamgLevel& C = a.lv[k + 1];
+        if (k + 1 == a.small_from && !group_sync(g)) return false;   // the first block's levels are done
+        const Exec x = exec_for(a, k, g);
+        if (x.active)
+            for (int i = x.first; i < L.n; i += x.stride) L.e[i] = C.e[L.agg[i]];
+        if (!exec_sync(x, g)) return false;
+        double v[2] = {0.0, 0.0};
+        if (x.active)
+            for (int i = x.first; i < L.n; i += x.stride) {
+                const double qi = gamg_amul_row(L, L.diag, L.upper, L.e, i);
+                v[0] = __fma_rn(L.e[i], L.r[i], v[0]);
+                v[1] = __fma_rn(L.e[i], qi, v[1]);
+            }
+        if (!exec_sum<2>(x, v, a, GS_A, g)) return false;
+        if (v[1] > 0.0) {
+            const double sc = v[0] / v[1];
+            if (x.active)
+                for (int i = x.first; i < L.n; i += x.stride) L.e[i] = __dmul_rn(L.e[i], sc);
+            if (!exec_sync(x, g)) return false;
+        }
+        for (int s = 0; s < kGamgPostSweeps; s++) {
+            if (x.active)
+                for (int i = x.first; i < L.n; i += x.stride) L.q[i] = gamg_amul_row(L, L.diag, L.upper, L.e, i);
+            if (!exec_sync(x, g)) return false;
+            if (x.active)
+                for (int i = x.first; i < L.n; i += x.stride)
+                    L.e[i] = __fma_rn(L.wrd[i], __dsub_rn(L.r[i], L.q[i]), L.e[i]);
+            if (!exec_sync(x, g)) return false;
+        }
+    }
+    if (a.nlev == 1 || a.small_from == 0) return group_sync(g);
+    return true;
+}
+
+__global__ void __launch_bounds__(1024, 1) k_gamg(GamgArgs a, unsigned long long timeout_ns)
+{
+    Group g{reinterpret_cast<unsigned*>(a.status + DS_BARRIER), a.status, (int)gridDim.x, (int)blockIdx.x, timeout_ns};
+    spuma_solver_perf pf{};
+    pf.n_levels = a.nlev;
+    const GamgLevel& L0 = a.lv[0];
+    struct {
+        int first, stride;
+    } it{g.bid * (int)blockDim.x + (int)threadIdx.x, g.nblocks * (int)blockDim.x};
+    bool ok = gamg_coarse_matrices(a, g);
+    // x, b, r = b - A x, normFactor (row sums of A times mean(x)), res0
+    double v[1] = {0.0};
+    if (ok) {
+        for (int i = it.first; i < L0.n; i += it.stride) {
+            a.x[i] = a.x_orig[i];
+            a.b[i] = a.b_orig[i];
+            v[0] += a.x[i];
+            if (!isfinite(a.b[i])) flag_error(a.status, SPUMA_ERR_NONFINITE, i);
+        }
+        block_reduce_store<1>(v, a.partials, GS_A, g.bid);
+        ok = group_sync(g);
+    }
+    double nfac = 1.0, res0 = 0.0, res = 0.0;
+    if (ok) {
+        double t[1];
+        grid_reduce_read<1>(t, a.partials, GS_A, g.nblocks);
+        const double xbar = L0.n > 0 ? t[0] / (double)L0.n : 0.0;
+        double acc[2] = {0.0, 0.0};
+        for (int i = it.first; i < L0.n; i += it.stride) {
+            const double q = gamg_amul_row(L0, L0.diag, L0.upper, a.x, i);
+            const double r = a.b[i] - q;
+            a.res[i] = r;
+            double s = L0.diag[i];
+            for (int e = L0.rptr[i]; e < L0.rptr[i + 1]; e++) s += L0.upper[L0.rfac[e]];
+            const double tt = s * xbar;
+            acc[0] += fabs(r);
+            acc[1] += fabs(q - tt) + fabs(a.b[i] - tt);
+        }
+        block_reduce_store<2>(acc, a.partials, GS_B, g.bid);
+        ok = group_sync(g);
+        if (ok) {
+            grid_reduce_read<2>(acc, a.partials, GS_B, g.nblocks);
+            nfac = acc[1] + 1e-20;
+            res0 = acc[0] / nfac;
+            res = res0;
+        }
+    }
+    auto conv = [&](double rr) { return rr < a.tol || (a.rel_tol > 0.0 && rr < a.rel_tol * res0); };
+    int n_it = 0;
+    if (ok && (a.min_iter > 0 || !conv(res0))) {
+        for (;;) {
+            ok = gamg_vcycle(a, g);
+            if (!ok) break;
+            double acc[1] = {0.0};
+            for (int i = it.first; i < L0.n; i += it.stride) a.x[i] = __dadd_rn(a.x[i], L0.e[i]);
+            ok = group_sync(g);
+            if (!ok) break;
+            for (int i = it.first; i < L0.n; i += it.stride) {
+                const double r = a.b[i] - gamg_amul_row(L0, L0.diag, L0.upper, a.x, i);
+                a.res[i] = r;
+                acc[0] += fabs(r);
+            }
+            block_reduce_store<1>(acc, a.partials, GS_C, g.bid);
+            ok = group_sync(g);
+            if (!ok) break;
+            grid_reduce_read<1>(acc, a.partials, GS_C, g.nblocks);
+            res = acc[0] / nfac;
+            n_it++;
+            if (!((n_it < a.max_iter && !conv(res)) || n_it < a.min_iter)) break;
+        }
+    }
+    if (ok)
+        for (int i = it.first; i < L0.n; i += it.stride) a.x_orig[i] = a.x[i];
+    if (g.bid == 0 && threadIdx.x == 0 && a.perf) {
+        pf.initial_residual = res0;
+        pf.final_residual = res;
+        pf.n_iter = n_it;
+        pf.converged = conv(res);
+        __threadfence();
+        pf.status = ld_volatile_int(a.status);
+        if (pf.status != 0) pf.converged = 0;
+        *a.perf = pf;
+    }
+}
+
+// ----------------------------------------------------------------- host ---
+struct GamgHostLevel {
+    int n = 0, nf = 0;
+    std::vector<int> l, u;                   // faces of this level (sorted by (l, u))
+    std::vector<int> rptr, rcol, rfac;       // row CSR
+    std::vector<int> agg, cptr, ccell, fptr, fface, iptr, iface;   // towards the next level
+};
+
+static void gamg_rows(GamgHostLevel& L)
+{
+    L.rptr.assign(L.n + 1, 0);
+    for (int f = 0; f < L.nf; f++) {
+        L.rptr[L.l[f] + 1]++;
+        L.rptr[L.u[f] + 1]++;
+    }
+    for (int i = 0; i < L.n; i++) L.rptr[i + 1] += L.rptr[i];
+    std::vector<int> cur(L.rptr.begin(), L.rptr.end() - 1);
+    L.rcol.resize(2 * (size_t)L.nf);
+    L.rfac.resize(2 * (size_t)L.nf);
+    for (int f = 0; f < L.nf; f++) {   // ascending f: each row's entries in face order
+        int a = L.l[f], b = L.u[f];
+        L.rcol[cur[a]] = b;
+        L.rfac[cur[a]++] = f;
+        L.rcol[cur[b]] = a;
+        L.rfac[cur[b]++] = f;
+    }
+}
+
+// One pairwise level; returns the next level's cell count.
+static int gamg_agglomerate(const GamgHostLevel& L, const std::vector<double>& w, std::vector<int>& agg)
+{
+    agg.assign(L.n, -1);
+    int nc = 0;
+    for (int i = 0; i < L.n; i++) {
+        if (agg[i] != -1) continue;
+        int best = -1;
+        double bw = -INFINITY;
+        for (int e = L.rptr[i]; e < L.rptr[i + 1]; e++) {
+            const int j = L.rcol[e], f = L.rfac[e];
+            if (agg[j] == -1 && w[f] > bw) {
+                best = j;
+                bw = w[f];
+            }
+        }
+        if (best >= 0) {
+            agg[i] = agg[best] = nc++;
+            continue;
+        }
+        bw = -INFINITY;
+        for (int e = L.rptr[i]; e < L.rptr[i + 1]; e++) {
+            const int j = L.rcol[e], f = L.rfac[e];
+            if (w[f] > bw) {
+                best = j;
+                bw = w[f];
+            }
+        }
+        agg[i] = best >= 0 ? agg[best] : nc++;
+    }
+    return nc;
+}
+
+}  // namespace spuma
+
+using namespace spuma;
+
+struct spuma_gamg {
+    spuma_ldu_t h = nullptr;
+    std::vector<GamgHostLevel> lv;
+    size_t bytes = 0;
+    char* ws = nullptr;
+    GamgLevel* dlv = nullptr;            // device descriptors
+    std::vector<GamgLevel> hlv;          // host copy of the descriptors
+    double *x = nullptr, *b = nullptr, *pw = nullptr, *pp = nullptr, *pq = nullptr, *px = nullptr;
+    double* partials = nullptr;
+    int small_from = 0;
+};
+
+namespace {
+
+size_t gamg_layout(spuma_gamg& G, bool assign)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = (off + bytes + 255) & ~(size_t)255;
+        return assign ? (void*)(G.ws + o) : nullptr;
+    };
+    const int L = (int)G.lv.size();
+    G.dlv = (GamgLevel*)take(sizeof(GamgLevel) * L);
+    G.hlv.assign(L, GamgLevel{});
+    for (int k = 0; k < L; k++) {
+        GamgHostLevel& H = G.lv[k];
+        GamgLevel& D = G.hlv[k];
+        D.n = H.n;
+        D.nf = H.nf;
+        D.rptr = (int*)take(4 * H.rptr.size());
+        D.rcol = (int*)take(4 * H.rcol.size() + 4);
+        D.rfac = (int*)take(4 * H.rfac.size() + 4);
+        if (k + 1 < L) {
+            D.agg = (int*)take(4 * H.agg.size() + 4);
+            D.cptr = (int*)take(4 * H.cptr.size());
+            D.ccell = (int*)take(4 * H.ccell.size() + 4);
+            D.fptr = (int*)take(4 * H.fptr.size());
+            D.fface = (int*)take(4 * H.fface.size() + 4);
+            D.iptr = (int*)take(4 * H.iptr.size());
+            D.iface = (int*)take(4 * H.iface.size() + 4);
+        }
+        if (k > 0) {
+            D.diag = (double*)take(8 * (size_t)H.n + 8);
+            D.upper = (double*)take(8 * (size_t)H.nf + 8);
+        }
+        D.wrd = (double*)take(8 * (size_t)H.n + 8);
+        D.r = (double*)take(8 * (size_t)H.n + 8);
+        D.e = (double*)take(8 * (size_t)H.n + 8);
+        D.q = (double*)take(8 * (size_t)H.n + 8);
+    }
+    for (int k = 0; k + 1 < L; k++) {
+        G.hlv[k].cdiag = const_cast<double*>(G.hlv[k + 1].diag);
+        G.hlv[k].cupper = const_cast<double*>(G.hlv[k + 1].upper);
+    }
+    const size_t n0 = G.lv[0].n, nc = G.lv.back().n;
+    G.x = (double*)take(8 * n0 + 8);
+    G.b = (double*)take(8 * n0 + 8);
+    G.pw = (double*)take(8 * nc + 8);
+    G.pp = (double*)take(8 * nc + 8);
+    G.pq = (double*)take(8 * nc + 8);
+    G.px = (double*)take(8 * nc + 8);
+    G.partials = (double*)take(8 * (size_t)kMaxBlocks * kSlots);
+    return off;
+}
+
+}  // namespace
+
+extern "C" {
+
+spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_stream_t stream, spuma_gamg_t* out)
+{
+    if (!out) { set_error("out is NULL"); return SPUMA_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!h || (h->nf > 0 && !face_weight)) {
+        set_error("spuma_gamg_create: bad argument");
+        return SPUMA_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    spuma_gamg* G = new spuma_gamg();
+    G->h = h;
+    GamgHostLevel L0;
+    L0.n = h->n;
+    L0.nf = h->nf;
+    L0.l.resize(h->nf);
+    L0.u.resize(h->nf);
+    std::vector<double> w(h->nf);
+    cudaError_t e = cudaSuccess;
+    if (h->nf > 0) {
+        e = cudaMemcpyAsync(L0.l.data(), h->at<int>(h->L.laddr), 4 * (size_t)h->nf, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(L0.u.data(), h->at<int>(h->L.uaddr), 4 * (size_t)h->nf, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(w.data(), face_weight, 8 * (size_t)h->nf, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        delete G;
+        return cuda_fail(e, "spuma_gamg_create: copy of the addressing");
+    }
+    G->lv.push_back(std::move(L0));
+    gamg_rows(G->lv[0]);
+    while ((int)G->lv.size() < kGamgMaxLevels && G->lv.back().n > kGamgCoarsest) {
+        GamgHostLevel& F = G->lv.back();
+        const int nc = gamg_agglomerate(F, w, F.agg);
+        if (nc >= F.n) break;
+        // coarse faces: (min, max) aggregate pairs, sorted, fine faces in ascending order
+        std::vector<std::pair<long long, int>> keyed;
+        keyed.reserve(F.nf);
+        for (int f = 0; f < F.nf; f++) {
+            const int a = F.agg[F.l[f]], b = F.agg[F.u[f]];
+            if (a != b) keyed.push_back({(long long)std::min(a, b) * nc + std::max(a, b), f});
+        }
+        std::stable_sort(keyed.begin(), keyed.end(),
+                         [](const std::pair<long long, int>& x, const std::pair<long long, int>& y) {
+                             return x.first < y.first;
+                         });
+        GamgHostLevel C;
+        C.n = nc;
+        F.fptr.assign(1, 0);
+        std::vector<double> wc;
+        for (size_t j = 0; j < keyed.size(); j++) {
+            if (j == 0 || keyed[j].first != keyed[j - 1].first) {
+                if (j > 0) F.fptr.push_back((int)j);
+                C.l.push_back((int)(keyed[j].first / nc));
+                C.u.push_back((int)(keyed[j].first % nc));
+                wc.push_back(0.0);
+            }
+            wc.back() += w[keyed[j].second];
+            F.fface.push_back(keyed[j].second);
+        }
+        F.fptr.push_back((int)keyed.size());
+        C.nf = (int)C.l.size();
+        // next-level cell -> cells, -> faces inside it (ascending)
+        F.cptr.assign(nc + 1, 0);
+        for (int i = 0; i < F.n; i++) F.cptr[F.agg[i] + 1]++;
+        for (int c = 0; c < nc; c++) F.cptr[c + 1] += F.cptr[c];
+        F.ccell.resize(F.n);
+        std::vector<int> cur(F.cptr.begin(), F.cptr.end() - 1);
+        for (int i = 0; i < F.n; i++) F.ccell[cur[F.agg[i]]++] = i;
+        F.iptr.assign(nc + 1, 0);
+        for (int f = 0; f < F.nf; f++)
+            if (F.agg[F.l[f]] == F.agg[F.u[f]]) F.iptr[F.agg[F.l[f]] + 1]++;
+        for (int c = 0; c < nc; c++) F.iptr[c + 1] += F.iptr[c];
+        F.iface.resize(F.iptr[nc]);
+        cur.assign(F.iptr.begin(), F.iptr.end() - 1);
+        for (int f = 0; f < F.nf; f++)
+            if (F.agg[F.l[f]] == F.agg[F.u[f]]) F.iface[cur[F.agg[F.l[f]]]++] = f;
+        gamg_rows(C);
+        G->lv.push_back(std::move(C));
+        w.swap(wc);
+    }
+    G->bytes = gamg_layout(*G, false);
+    G->small_from = (int)G->lv.size();
+    for (int k = 0; k < (int)G->lv.size(); k++)
+        if (G->lv[k].n <= 2048) {
+            G->small_from = k;
+            break;
+        }
+    *out = G;
+    return SPUMA_OK;
+}
+
+size_t spuma_gamg_workspace_bytes(spuma_gamg_t g) { return g ? g->bytes : 0; }
+
+spuma_status spuma_gamg_bind(spuma_gamg_t g, void* workspace, size_t workspace_bytes, spuma_stream_t stream)
+{
+    if (!g || !workspace || ((uintptr_t)workspace & 255u) != 0) {
+        set_error("spuma_gamg_bind: bad argument (workspace must be 256-byte aligned)");
+        return SPUMA_ERR_INVALID_ARG;
+    }
+    if (workspace_bytes < g->bytes) {
+        set_error("spuma_gamg_bind: workspace needs " + std::to_string(g->bytes) + " bytes");
+        return SPUMA_ERR_WORKSPACE_TOO_SMALL;
+    }
+    g->ws = (char*)workspace;
+    gamg_layout(*g, true);
+    cudaStream_t s = (cudaStream_t)stream;
+    auto up = [&](const void* dst, const std::vector<int>& v) {
+        return v.empty() ? cudaSuccess
+                         : cudaMemcpyAsync((void*)dst, v.data(), 4 * v.size(), cudaMemcpyHostToDevice, s);
+    };
+    for (size_t k = 0; k < g->lv.size(); k++) {
+        const GamgHostLevel& H = g->lv[k];
+        const GamgLevel& D = g->hlv[k];
+        SPUMA_CUDA(up(D.rptr, H.rptr));
+        SPUMA_CUDA(up(D.rcol, H.rcol));
+        SPUMA_CUDA(up(D.rfac, H.rfac));
+        if (k + 1 < g->lv.size()) {
+            SPUMA_CUDA(up(D.agg, H.agg));
+            SPUMA_CUDA(up(D.cptr, H.cptr));
+            SPUMA_CUDA(up(D.ccell, H.ccell));
+            SPUMA_CUDA(up(D.fptr, H.fptr));
+            SPUMA_CUDA(up(D.fface, H.fface));
+            SPUMA_CUDA(up(D.iptr, H.iptr));
+            SPUMA_CUDA(up(D.iface, H.iface));
+        }
+    }
+    SPUMA_CUDA(cudaStreamSynchronize(s));
+    return SPUMA_OK;
+}
+
+spuma_status spuma_gamg_info(spuma_gamg_t g, int32_t* n_levels, int32_t* level_cells, int32_t max_levels)
+{
+    if (!g) { set_error("spuma_gamg_info: handle is NULL"); return SPUMA_ERR_INVALID_ARG; }
+    if (n_levels) *n_levels = (int32_t)g->lv.size();
+    if (level_cells)
+        for (int k = 0; k < (int)g->lv.size() && k < max_levels; k++) level_cells[k] = g->lv[k].n;
+    return SPUMA_OK;
+}
+
+spuma_status spuma_gamg_solve(spuma_gamg_t g, const double* diag, const double* upper, const double* b, double* x,
+                              const spuma_solver_controls* ctl, spuma_solver_perf* perf, spuma_stream_t stream)
+{
+    if (!g || !g->ws || !ctl || !(ctl->tolerance >= 0.0) || !(ctl->rel_tol >= 0.0) || ctl->max_iter < 0 ||
+        ctl->min_iter < 0 || ctl->precision != SPUMA_F64 || (g->h->n > 0 && (!diag || !b || !x)) ||
+        (g->h->nf > 0 && !upper)) {
+        set_error("spuma_gamg_solve: bad argument (bound solver, precision F64)");
+        return SPUMA_ERR_INVALID_ARG;
+    }
+    spuma_ldu_t h = g->h;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->n == 0) {
+        if (perf) {
+            spuma_solver_perf z{};
+            z.converged = 1;
+            SPUMA_CUDA(cudaMemcpyAsync(perf, &z, sizeof(z), cudaMemcpyHostToDevice, s));
+        }
+        return SPUMA_OK;
+    }
+    g->hlv[0].diag = diag;
+    g->hlv[0].upper = upper;
+    SPUMA_CUDA(cudaMemcpyAsync(g->dlv, g->hlv.data(), sizeof(GamgLevel) * g->hlv.size(), cudaMemcpyHostToDevice, s));
+    GamgArgs a{};
+    a.nlev = (int)g->lv.size();
+    a.small_from = g->small_from;
+    a.lv = g->dlv;
+    a.b_orig = b;
+    a.x_orig = x;
+    a.x = g->x;
+    a.b = g->b;
+    a.res = g->hlv[0].r;
+    a.pw = g->pw;
+    a.pp = g->pp;
+    a.pq = g->pq;
+    a.px = g->px;
+    a.partials = g->partials;
+    a.status = h->at<int>(h->L.status);
+    a.perf = perf;
+    a.max_iter = ctl->max_iter;
+    a.min_iter = ctl->min_iter;
+    a.tol = ctl->tolerance;
+    a.rel_tol = ctl->rel_tol;
+    int per_sm = 0;
+    SPUMA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gamg, 1024, 0));
+    if (per_sm < 1) { set_error("GAMG kernel cannot be resident"); return SPUMA_ERR_CUDA; }
+    const int64_t want = ((int64_t)h->n + 1023) / 1024;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, std::min<int64_t>((int64_t)per_sm * h->num_sms,
+                                                                                          kMaxBlocks)));
+    SPUMA_CUDA(cudaMemsetAsync(h->at<char>(h->L.bar), 0, h->L.status + 256 - h->L.bar, s));
+    unsigned long long tns = barrier_timeout_ns();
+    void* args[] = {(void*)&a, (void*)&tns};
+    SPUMA_CUDA(cudaLaunchCooperativeKernel((const void*)k_gamg, grid, 1024, args, 0, s));
+    count_launch();
+    return SPUMA_OK;
+}
+
+spuma_status spuma_gamg_destroy(spuma_gamg_t g)
+{
+    delete g;
+    return SPUMA_OK;
+}
+
+}  // extern "C"
