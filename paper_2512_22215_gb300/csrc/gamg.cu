@@ -52,6 +52,7 @@ struct GamgLevel {
     const double *diag, *upper;             // A_k (level 0: the caller's arrays)
     double *cdiag, *cupper;                 // A_{k+1} written here (k < L-1)
     double *wrd;                            // omega / diag
+    double *rval;                           // A_k's off-diagonal coefficients in row-CSR order (per solve)
     double *r, *e, *q;                      // right-hand side, correction, scratch
 };
 
@@ -109,11 +110,28 @@ __device__ __forceinline__ bool exec_sum(const Exec& x, double (&v)[NV], const G
     return true;
 }
 
-__device__ __forceinline__ double gamg_amul_row(const GamgLevel& L, const double* d, const double* up,
-                                                const double* x, int i)
+// (A_k x)_i: d_i x_i, then the row's entries in face order, one FMA each;
+// entries loaded in groups of 8 (columns and coefficients, then the
+// gathers), the FMAs in entry order.
+__device__ __forceinline__ double gamg_amul_row(const GamgLevel& L, const double* d, const double* x, int i)
 {
     double y = __dmul_rn(d[i], x[i]);
-    for (int e = L.rptr[i]; e < L.rptr[i + 1]; e++) y = __fma_rn(up[L.rfac[e]], x[L.rcol[e]], y);
+    const int e1 = L.rptr[i + 1];
+    for (int e0 = L.rptr[i]; e0 < e1; e0 += 8) {
+        int c[8];
+        double v[8], xv[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const bool ok = e0 + j < e1;
+            c[j] = ok ? __ldg(L.rcol + e0 + j) : -1;
+            v[j] = ok ? L.rval[e0 + j] : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++) xv[j] = c[j] >= 0 ? x[c[j]] : 0.0;
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            if (c[j] >= 0) y = __fma_rn(v[j], xv[j], y);
+    }
     return y;
 }
 
@@ -145,6 +163,7 @@ __device__ bool gamg_coarse_matrices(const GamgArgs& a, const Group& g)
     for (int k = 0; k < a.nlev; k++) {
         const GamgLevel& L = a.lv[k];
         for (int i = first; i < L.n; i += stride) L.wrd[i] = __dmul_rn(kGamgOmega, __ddiv_rn(1.0, L.diag[i]));
+        for (int e = first; e < 2 * L.nf; e += stride) L.rval[e] = L.upper[L.rfac[e]];
     }
     return group_sync(g);
 }
@@ -192,7 +211,7 @@ __device__ bool gamg_coarsest(const GamgArgs& a, const Group& g)
             double s[1] = {0.0};
             if (x.active)
                 for (int i = x.first; i < L.n; i += x.stride) {
-                    const double qi = gamg_amul_row(L, L.diag, L.upper, p, i);
+                    const double qi = gamg_amul_row(L, L.diag, p, i);
                     q[i] = qi;
                     s[0] = __fma_rn(qi, p[i], s[0]);
                 }
@@ -242,7 +261,7 @@ __device__ bool gamg_vcycle(const GamgArgs& a, const Group& g)
         double v[2] = {0.0, 0.0};
         if (x.active)
             for (int i = x.first; i < L.n; i += x.stride) {
-                const double qi = gamg_amul_row(L, L.diag, L.upper, L.e, i);
+                const double qi = gamg_amul_row(L, L.diag, L.e, i);
                 v[0] = __fma_rn(L.e[i], L.r[i], v[0]);
                 v[1] = __fma_rn(L.e[i], qi, v[1]);
             }
@@ -253,13 +272,14 @@ __device__ bool gamg_vcycle(const GamgArgs& a, const Group& g)
                 for (int i = x.first; i < L.n; i += x.stride) L.e[i] = __dmul_rn(L.e[i], sc);
             if (!exec_sync(x, g)) return false;
         }
+        // Jacobi sweeps alternate between e and q (an even count ends in e)
+        static_assert(kGamgPostSweeps % 2 == 0, "sweeps alternate e -> q -> e");
         for (int s = 0; s < kGamgPostSweeps; s++) {
-            if (x.active)
-                for (int i = x.first; i < L.n; i += x.stride) L.q[i] = gamg_amul_row(L, L.diag, L.upper, L.e, i);
-            if (!exec_sync(x, g)) return false;
+            const double* src = (s & 1) ? L.q : L.e;
+            double* dst = (s & 1) ? L.e : L.q;
             if (x.active)
                 for (int i = x.first; i < L.n; i += x.stride)
-                    L.e[i] = __fma_rn(L.wrd[i], __dsub_rn(L.r[i], L.q[i]), L.e[i]);
+                    dst[i] = __fma_rn(L.wrd[i], __dsub_rn(L.r[i], gamg_amul_row(L, L.diag, src, i)), src[i]);
             if (!exec_sync(x, g)) return false;
         }
     }
@@ -296,11 +316,11 @@ __global__ void __launch_bounds__(1024, 1) k_gamg(GamgArgs a, unsigned long long
         const double xbar = L0.n > 0 ? t[0] / (double)L0.n : 0.0;
         double acc[2] = {0.0, 0.0};
         for (int i = it.first; i < L0.n; i += it.stride) {
-            const double q = gamg_amul_row(L0, L0.diag, L0.upper, a.x, i);
+            const double q = gamg_amul_row(L0, L0.diag, a.x, i);
             const double r = a.b[i] - q;
             a.res[i] = r;
             double s = L0.diag[i];
-            for (int e = L0.rptr[i]; e < L0.rptr[i + 1]; e++) s += L0.upper[L0.rfac[e]];
+            for (int e = L0.rptr[i]; e < L0.rptr[i + 1]; e++) s += L0.rval[e];
             const double tt = s * xbar;
             acc[0] += fabs(r);
             acc[1] += fabs(q - tt) + fabs(a.b[i] - tt);
@@ -325,7 +345,7 @@ __global__ void __launch_bounds__(1024, 1) k_gamg(GamgArgs a, unsigned long long
             ok = group_sync(g);
             if (!ok) break;
             for (int i = it.first; i < L0.n; i += it.stride) {
-                const double r = a.b[i] - gamg_amul_row(L0, L0.diag, L0.upper, a.x, i);
+                const double r = a.b[i] - gamg_amul_row(L0, L0.diag, a.x, i);
                 a.res[i] = r;
                 acc[0] += fabs(r);
             }
@@ -464,6 +484,7 @@ size_t gamg_layout(spuma_gamg& G, bool assign)
             D.upper = (double*)take(8 * (size_t)H.nf + 8);
         }
         D.wrd = (double*)take(8 * (size_t)H.n + 8);
+        D.rval = (double*)take(16 * (size_t)H.nf + 8);
         D.r = (double*)take(8 * (size_t)H.n + 8);
         D.e = (double*)take(8 * (size_t)H.n + 8);
         D.q = (double*)take(8 * (size_t)H.n + 8);
