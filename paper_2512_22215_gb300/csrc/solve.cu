@@ -386,12 +386,15 @@ __device__ __forceinline__ void vadd_abs(A& acc, double2 r)
     acc.add(fabs(r.y));
 }
 // ------------------------------------------------------------ phases --------
+__device__ __forceinline__ void gather_symmetric(const SolveArgs& a, const RowIter& it, bool& bad);
+
 // Gather the LDU coefficients into the internal layout (+ FP32 copies).
+template <bool ASYM>
 __device__ bool phase_gather(const SolveArgs& a, const Group& g)
 {
     RowIter it = rows_of(g);
     bool bad = false;
-    if (a.lower_orig) {
+    if constexpr (ASYM) {
         // asymmetric: row u's lower entry of face f holds lower_f (A) and
         // upper_f (A^T), row l's upper entry upper_f (A) and lower_f (A^T)
         for (int e = it.first; e < a.nf; e += it.stride) {
@@ -409,9 +412,17 @@ __device__ bool phase_gather(const SolveArgs& a, const Group& g)
             a.d64[p] = dv;
             bad |= !isfinite(dv);
         }
-        if (bad) flag_error(a.status, SPUMA_ERR_NONFINITE, -1);
-        return group_sync(g);
+    } else {
+        gather_symmetric(a, it, bad);
     }
+    if (bad) flag_error(a.status, SPUMA_ERR_NONFINITE, -1);
+    return group_sync(g);
+}
+
+// Symmetric gather: a_f into the internal CSR (+ FP32 copies), the diagonal,
+// and the fixed-width Amul layout's coefficients.
+__device__ __forceinline__ void gather_symmetric(const SolveArgs& a, const RowIter& it, bool& bad)
+{
     for (int e = it.first; e < a.nf; e += it.stride) {
         double lv = a.upper_orig[a.Lface[e]];
         double uv = a.upper_orig[a.Uface[e]];
@@ -436,17 +447,16 @@ __device__ bool phase_gather(const SolveArgs& a, const Group& g)
             }
         }
     }
-    if (bad) flag_error(a.status, SPUMA_ERR_NONFINITE, -1);
-    return group_sync(g);
 }
 
 // DIC pivots level by level: p_i = d_i - sum_{lower entries} (a a)/p_col,
 // then rD = 1/p and the sweep coefficients rD_row * a (+ FP32 copies).
 // Diagonal: rD = 1/d.
+template <bool ASYM>
 __device__ bool phase_factor(const SolveArgs& a, const Group& g)
 {
     RowIter it = rows_of(g);
-    if (a.precond == SPUMA_PRECOND_DILU) {
+    if (ASYM && a.precond == SPUMA_PRECOND_DILU) {
         // DILU pivots, level by level: p_u -= (upper_f lower_f) / p_l in face order
         for (int L = 0; L < a.nlev; L++) {
             const int r0 = a.lvl[L], r1 = a.lvl[L + 1];
@@ -516,10 +526,15 @@ __device__ bool phase_factor(const SolveArgs& a, const Group& g)
 }
 
 // ------------------------------------------------------ DIC sweeps ---------
+// What the sweeps' reduction takes: rho = w.r (PCG), rho = w.dotv with a
+// vector of the caller's (PBiCG: wA.rT), or nothing (PBiCG's M^-T apply).
+// A template argument, so that the PCG kernels keep their own code.
+enum RhoWith { RHO_R = 0, RHO_VEC = 1, RHO_NONE = 2 };
+
 // Forward rows of one level: w = rD r - sum (rD a) w_lower (ascending face
 // order); with `rho` (top level: no upper neighbours, so w is final here)
-// also rho += w dotv.
-template <class T>
+// also rho += w r (or w dotv).
+template <class T, int RW>
 __device__ __forceinline__ void fwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int r1, int first, int stride, bool rho,
                                          const T* dotv, Acc<T>& arho)
 {
@@ -541,14 +556,14 @@ __device__ __forceinline__ void fwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int
         for (int k = 0; k < R; k++)
             if (p[k] < r1) {
                 v.w[p[k]] = ww[k];
-                if (rho) arho.prod(ww[k], dotv == v.r ? rr[k] : dotv[p[k]]);
+                if (RW != RHO_NONE && rho) arho.prod(ww[k], RW == RHO_R ? rr[k] : dotv[p[k]]);
             }
     }
 }
 
 // Backward rows of one level: w -= sum (rD a) w_upper (descending face
-// order); rho += w dotv (dotv may be NULL).
-template <class T>
+// order); rho += w r (or w dotv).
+template <class T, int RW>
 __device__ __forceinline__ void bwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int r1, int first, int stride,
                                          const T* dotv, Acc<T>& arho)
 {
@@ -569,30 +584,29 @@ __device__ __forceinline__ void bwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int
         for (int k = 0; k < R; k++)
             if (p[k] < r1) {
                 v.w[p[k]] = ww[k];
-                if (dotv) arho.prod(ww[k], dotv[p[k]]);
+                if (RW != RHO_NONE) arho.prod(ww[k], RW == RHO_R ? v.r[p[k]] : dotv[p[k]]);
             }
     }
 }
 
 // w = M^-1 r with the DIC (or DILU) factor held in A's sweep coefficients,
-// and the block partials of rho = w.dotv (dotv = r by default) in `slot`
-// before the last grid barrier (slot < 0: no rho).  Forward sweep over levels 0 ..
-// nlev-1, backward over nlev-2 .. 0 (the top level has no upper neighbours:
-// its backward step would leave w as it is, so its rho terms are taken in the
-// forward step), one grid barrier per level.  The small last levels
-// (level >= tail_from) run on the group's first block alone, forward then
-// backward, with block-level barriers and one grid barrier after them.
-template <class T>
+// and the block partials of rho (RhoWith) in `slot` before the last grid
+// barrier.  Forward sweep over levels 0 .. nlev-1, backward over nlev-2 .. 0
+// (the top level has no upper neighbours: its backward step would leave w
+// as it is, so its rho terms are taken in the forward step), one grid
+// barrier per level.  The small last levels (level >= tail_from) run on the
+// group's first block alone, forward then backward, with block-level
+// barriers and one grid barrier after them.
+template <class T, int RW = RHO_R>
 __device__ bool dic_apply(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const Group& g, PhaseClock& pc,
                           const T* dotv = nullptr, int slot = SL_B)
 {
     const RowIter it = rows_of(g);
     const int nlev = a.nlev, tail = min(a.tail_from, nlev);
     const int tid = (int)threadIdx.x, bs = (int)blockDim.x;
-    if (!dotv && slot >= 0) dotv = v.r;
     Acc<T> arho;
     auto end_step = [&](bool last) {
-        if (last && slot >= 0) {
+        if (RW != RHO_NONE && last) {
             double t[1] = {arho.value()};
             block_reduce_store<1>(t, a.partials, slot, g.bid);
         }
@@ -600,18 +614,18 @@ __device__ bool dic_apply(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const 
     };
     if (nlev == 0) return end_step(true);
     for (int L = 0; L < tail; L++) {
-        fwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], it.first, it.stride, L == nlev - 1 && dotv, dotv, arho);
+        fwd_rows<T, RW>(A, v, a.lvl[L], a.lvl[L + 1], it.first, it.stride, L == nlev - 1, dotv, arho);
         if (!end_step(nlev == 1)) return false;
         pc.lap(CK_FWD + min(L, 63));
     }
     if (tail < nlev) {
         if (g.bid == 0) {
             for (int L = tail; L < nlev; L++) {
-                fwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], tid, bs, L == nlev - 1 && dotv, dotv, arho);
+                fwd_rows<T, RW>(A, v, a.lvl[L], a.lvl[L + 1], tid, bs, L == nlev - 1, dotv, arho);
                 __syncthreads();
             }
             for (int L = nlev - 2; L >= tail; L--) {
-                bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], tid, bs, dotv, arho);
+                bwd_rows<T, RW>(A, v, a.lvl[L], a.lvl[L + 1], tid, bs, dotv, arho);
                 __syncthreads();
             }
         }
@@ -619,7 +633,7 @@ __device__ bool dic_apply(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const 
         pc.lap(CK_FWD + min(tail, 63));
     }
     for (int L = min(tail, nlev - 1) - 1; L >= 0; L--) {
-        bwd_rows<T>(A, v, a.lvl[L], a.lvl[L + 1], it.first, it.stride, dotv, arho);
+        bwd_rows<T, RW>(A, v, a.lvl[L], a.lvl[L + 1], it.first, it.stride, dotv, arho);
         if (!end_step(L == 0)) return false;
         pc.lap(CK_BWD + min(L, 63));
     }
@@ -1065,8 +1079,8 @@ __device__ bool solve_pbicg(const SolveArgs& a, const Group& g, double nfac, dou
             }
             wArA_old = wArA;
             if (a.precond == SPUMA_PRECOND_DILU) {
-                if (!dic_apply<double>(a, A, Vecs<double>{x, rA, wA, pA, wT}, g, pc, rT, SL_B)) return false;
-                if (!dic_apply<double>(a, AT, Vecs<double>{x, rT, wT, pT, wA}, g, pc, nullptr, -1)) return false;
+                if (!dic_apply<double, RHO_VEC>(a, A, Vecs<double>{x, rA, wA, pA, wT}, g, pc, rT, SL_B)) return false;
+                if (!dic_apply<double, RHO_NONE>(a, AT, Vecs<double>{x, rT, wT, pT, wA}, g, pc)) return false;
             } else {
                 double acc[1] = {0.0};
                 for (int p = it.first; p < a.n; p += it.stride) {
@@ -1135,8 +1149,8 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
     pf.n_levels = a.nlev;
     bool ok = true;
     if (a.mode == MODE_PREPARE || a.mode == MODE_SOLVE) {
-        ok = phase_gather(a, g);
-        if (ok) ok = phase_factor(a, g);
+        ok = phase_gather<KIND == KIND_PBICG>(a, g);
+        if (ok) ok = phase_factor<KIND == KIND_PBICG>(a, g);
     }
     if (KIND == KIND_SETUP && ok && a.mode == MODE_PRECONDITION) {
         // w = M^-1 r for r = b_orig, written to x_orig (FP64)
