@@ -568,15 +568,31 @@ __device__ __forceinline__ void bwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int
                                          const T* dotv, Acc<T>& arho)
 {
     constexpr int R = ChainShape<T>::R, G = ChainShape<T>::G;
+    // row extents one round ahead: the next round's are loaded while this
+    // round's entries and gathers are in flight (measured: backward sweep
+    // 135 -> 128 us per FP32 iteration at 200^3; no gain in the forward one)
+    int e0n[R], e1n[R];
+#pragma unroll
+    for (int k = 0; k < R; k++) {
+        const int pn = r0 + first + k * stride;
+        e0n[k] = pn < r1 ? __ldg(A.Uptr + pn) : 0;
+        e1n[k] = pn < r1 ? __ldg(A.Uptr + pn + 1) : 0;
+    }
     for (int pb = r0 + first; pb < r1; pb += R * stride) {
         int p[R], e0[R], e1[R];
         T ww[R];
 #pragma unroll
         for (int k = 0; k < R; k++) {
             p[k] = pb + k * stride;
+            e0[k] = e0n[k];
+            e1[k] = e1n[k];
+            const int pn = pb + (R + k) * stride;
+            e0n[k] = pn < r1 ? __ldg(A.Uptr + pn) : 0;
+            e1n[k] = pn < r1 ? __ldg(A.Uptr + pn + 1) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < R; k++) {
             const bool ok = p[k] < r1;
-            e0[k] = ok ? __ldg(A.Uptr + p[k]) : 0;
-            e1[k] = ok ? __ldg(A.Uptr + p[k] + 1) : 0;
             ww[k] = ok ? v.w[p[k]] : T(0);
         }
         rows_chain<T, R, G, true, true>(ww, e0, e1, A.Ucol, A.Uc, v.w);
