@@ -31,8 +31,8 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # the mixed-precision solve kernel on this workload, from the one-pass ncu
 # capture summarised in profiles/k_solve_mixed_200cubed_dram.md; valid only
 # for the solver source it was taken with (checked by hash, else null).
-TRAFFIC = {"solve_cu_sha1": "0b163b3a1ed7c8d2daf97beb42ee36572aeb0b1a",
-           "bytes_per_launch": 977370608128 + 148275682560}
+TRAFFIC = {"solve_cu_sha1": "0d727cfd6ca71709f3ca25a924ed607173cdc6dd",
+           "bytes_per_launch": 983751297280 + 150647074816}
 # Iteration counts of this seeded workload (mixed: inner iterations, outer
 # steps), used only to project the CPU oracle's bounded sample to a full solve.
 PROJECTION_ITERS = {"inner": 795, "outer": 5}
