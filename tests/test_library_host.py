@@ -127,3 +127,34 @@ def test_python_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(M, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         M.lib()
+
+
+def test_new_entry_points_reject_bad_arguments(L):
+    """The pressure step, the assembly adjoint, PBiCG and GAMG validate their
+    arguments on the host (no device call)."""
+    from paper_2512_22215_gb300._lib import Controls
+    ctl = Controls(3, 0, 1e-8, 0.0, 1e-4, 100, 0, 10, 0)
+    assert L.spuma_pbicg_solve(None, None, None, None, None, None, C.byref(ctl), None, None) == 1
+    assert L.spuma_fv_weights(None, None, None, None, None, None) == 1
+    assert L.spuma_fv_grad(None, None, None, None, 0, None, None, None, None, None, None) == 1
+    assert L.spuma_pressure_rhs(None, None, None, None, None, None, None, 0, None, None, None, None, None) == 1
+    assert L.spuma_pressure_flux(None, None, None, None, None, 0, None, None, None, None, None, None, None,
+                                 None, None, None) == 1
+    assert L.spuma_fv_div(None, None, 0, None, None, None, None) == 1
+    assert L.spuma_assemble_laplacian_adjoint(None, None, None, 0, None, None, None, None, None, None, None, None,
+                                              None) == 1
+    g = C.c_void_p()
+    assert L.spuma_gamg_create(None, None, None, C.byref(g)) == 1
+    assert L.spuma_gamg_create(None, None, None, None) == 1
+    assert L.spuma_gamg_workspace_bytes(None) == 0
+    assert L.spuma_gamg_bind(None, None, 0, None) == 1
+    assert L.spuma_gamg_solve(None, None, None, None, None, C.byref(ctl), None, None) == 1
+    assert L.spuma_gamg_info(None, None, None, 0) == 1
+    assert L.spuma_gamg_destroy(None) == 0
+
+
+def test_asymmetric_workspace_is_larger(L):
+    n, f = 1000, 2700
+    sym = L.spuma_workspace_bytes(n, f, 0)
+    asym = L.spuma_workspace_bytes(n, f, 1)
+    assert asym >= sym + 32 * f + 8 * n
