@@ -104,7 +104,10 @@ class ClockSampler:
     """nvidia-smi clock / throttle samples while the timed region runs."""
 
     def __init__(self, index: int):
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # SPUMA_CLOCKS_DIR keeps the raw samples (default: the system temporary directory)
+        import tempfile
+        self.path = os.path.join(os.environ.get("SPUMA_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"spuma_clocks_{os.getpid()}.csv")
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
