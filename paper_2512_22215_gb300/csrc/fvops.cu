@@ -84,21 +84,51 @@ __global__ void k_fv_grad(int n, const int* __restrict__ lo_start, const int* __
                           const double* __restrict__ bsf, const int8_t* __restrict__ btype,
                           const double* __restrict__ v, double* __restrict__ grad)
 {
+    constexpr int G = 4;   // faces whose loads are issued together
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double g[3] = {0.0, 0.0, 0.0};
         const double pi = p[i];
-        for (int k = lo_start[i]; k < lo_start[i + 1]; k++) {   // i = u(f)
-            const int f = lo_face[k];
-            const double wf = w[f];
-            const double pf = __dadd_rn(__dmul_rn(wf, p[l[f]]), __dmul_rn(__dsub_rn(1.0, wf), pi));
+        const int k1 = lo_start[i + 1];
+        for (int k0 = lo_start[i]; k0 < k1; k0 += G) {   // i = u(f)
+            int f[G];
+            double wf[G], po[G], s[G][3];
 #pragma unroll
-            for (int d = 0; d < 3; d++) g[d] = __dsub_rn(g[d], __dmul_rn(sf[3 * (size_t)f + d], pf));
+            for (int j = 0; j < G; j++) f[j] = k0 + j < k1 ? lo_face[k0 + j] : -1;
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+                const bool ok = f[j] >= 0;
+                wf[j] = ok ? w[f[j]] : 0.0;
+                po[j] = ok ? p[l[f[j]]] : 0.0;
+#pragma unroll
+                for (int d = 0; d < 3; d++) s[j][d] = ok ? sf[3 * (size_t)f[j] + d] : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < G; j++)
+                if (f[j] >= 0) {
+                    const double pf = __dadd_rn(__dmul_rn(wf[j], po[j]), __dmul_rn(__dsub_rn(1.0, wf[j]), pi));
+#pragma unroll
+                    for (int d = 0; d < 3; d++) g[d] = __dsub_rn(g[d], __dmul_rn(s[j][d], pf));
+                }
         }
-        for (int f = own_start[i]; f < own_start[i + 1]; f++) {  // i = l(f)
-            const double wf = w[f];
-            const double pf = __dadd_rn(__dmul_rn(wf, pi), __dmul_rn(__dsub_rn(1.0, wf), p[u[f]]));
+        const int f1 = own_start[i + 1];
+        for (int f0 = own_start[i]; f0 < f1; f0 += G) {  // i = l(f)
+            double wf[G], po[G], s[G][3];
 #pragma unroll
-            for (int d = 0; d < 3; d++) g[d] = __dadd_rn(g[d], __dmul_rn(sf[3 * (size_t)f + d], pf));
+            for (int j = 0; j < G; j++) {
+                const int f = f0 + j;
+                const bool ok = f < f1;
+                wf[j] = ok ? w[f] : 0.0;
+                po[j] = ok ? p[u[f]] : 0.0;
+#pragma unroll
+                for (int d = 0; d < 3; d++) s[j][d] = ok ? sf[3 * (size_t)f + d] : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < G; j++)
+                if (f0 + j < f1) {
+                    const double pf = __dadd_rn(__dmul_rn(wf[j], pi), __dmul_rn(__dsub_rn(1.0, wf[j]), po[j]));
+#pragma unroll
+                    for (int d = 0; d < 3; d++) g[d] = __dadd_rn(g[d], __dmul_rn(s[j][d], pf));
+                }
         }
         if (bstart) {
             for (int k = bstart[i]; k < bstart[i + 1]; k++) {
@@ -156,20 +186,39 @@ __global__ void k_fv_cell_sum(int n, const int* __restrict__ lo_start, const int
                               const double* __restrict__ phi, const int* __restrict__ bstart,
                               const int* __restrict__ blist, const double* __restrict__ bphi, double* __restrict__ out)
 {
+    constexpr int G = 4;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double acc = 0.0;
-        if (corr) {
-            for (int k = lo_start[i]; k < lo_start[i + 1]; k++) {
-                const int f = lo_face[k];
-                acc = __dsub_rn(acc, __dsub_rn(corr[f], phi[f]));
+        const int k1 = lo_start[i + 1], f1 = own_start[i + 1];
+        // neighbour-side faces subtract, owner-side faces add; with corr the
+        // face term is corr_f - phi_f, else phi_f; loads issued G at a time
+        for (int k0 = lo_start[i]; k0 < k1; k0 += G) {
+            int f[G];
+            double t[G];
+#pragma unroll
+            for (int j = 0; j < G; j++) f[j] = k0 + j < k1 ? lo_face[k0 + j] : -1;
+#pragma unroll
+            for (int j = 0; j < G; j++)
+                t[j] = f[j] < 0 ? 0.0 : (corr ? __dsub_rn(corr[f[j]], phi[f[j]]) : phi[f[j]]);
+#pragma unroll
+            for (int j = 0; j < G; j++)
+                if (f[j] >= 0) acc = __dsub_rn(acc, t[j]);
+        }
+        for (int f0 = own_start[i]; f0 < f1; f0 += G) {
+            double t[G];
+#pragma unroll
+            for (int j = 0; j < G; j++) {
+                const int f = f0 + j;
+                t[j] = f >= f1 ? 0.0 : (corr ? __dsub_rn(corr[f], phi[f]) : phi[f]);
             }
-            for (int f = own_start[i]; f < own_start[i + 1]; f++) acc = __dadd_rn(acc, __dsub_rn(corr[f], phi[f]));
-            if (bstart)
+#pragma unroll
+            for (int j = 0; j < G; j++)
+                if (f0 + j < f1) acc = __dadd_rn(acc, t[j]);
+        }
+        if (bstart) {
+            if (corr)
                 for (int k = bstart[i]; k < bstart[i + 1]; k++) acc = __dsub_rn(acc, bphi[blist[k]]);
-        } else {
-            for (int k = lo_start[i]; k < lo_start[i + 1]; k++) acc = __dsub_rn(acc, phi[lo_face[k]]);
-            for (int f = own_start[i]; f < own_start[i + 1]; f++) acc = __dadd_rn(acc, phi[f]);
-            if (bstart)
+            else
                 for (int k = bstart[i]; k < bstart[i + 1]; k++) acc = __dadd_rn(acc, bphi[blist[k]]);
         }
         out[i] = acc;
