@@ -31,8 +31,8 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # the mixed-precision solve kernel on this workload, from the one-pass ncu
 # capture summarised in profiles/k_solve_mixed_200cubed_dram.md; valid only
 # for the solver source it was taken with (checked by hash, else null).
-TRAFFIC = {"solve_cu_sha1": "0d727cfd6ca71709f3ca25a924ed607173cdc6dd",
-           "bytes_per_launch": 983751297280 + 150647074816}
+TRAFFIC = {"solve_cu_sha1": "df69578ba35d147967c81fadb3c1eb11e4da4b3a",
+           "bytes_per_launch": 835452662528 + 132145155840}
 # Iteration counts of this seeded workload (mixed: inner iterations, outer
 # steps), used only to project the CPU oracle's bounded sample to a full solve.
 PROJECTION_ITERS = {"inner": 795, "outer": 5}
@@ -358,6 +358,9 @@ def main():
         perf_h.copy_(perf, non_blocking=True)
 
     e2e_step()
+    # sampled like the timed steps (the same settle time after the sampler starts)
+    clocks_e2e = ClockSampler(local)
+    time.sleep(0.3)
     barrier()
     a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(s)
@@ -365,6 +368,7 @@ def main():
         e2e_step()
     c.record(s)
     c.synchronize()
+    clk_e2e = clocks_e2e.stop()
     e2e_ms = reduce_max(a.elapsed_time(c) / args.steps, world, dev)
     h2d = gamma_h.numel() * 8 + b_h.numel() * 8
     d2h = x_h.numel() * 8 + perf_h.numel()
@@ -573,7 +577,8 @@ def main():
         "roofline": roofline,
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "api": "spuma_assemble_laplacian + spuma_pcg_solve with gamma and b copied from pinned host "
-                       "memory and x and the solver report copied back, every step"},
+                       "memory and x and the solver report copied back, every step",
+                "clocks": clk_e2e},
         "gpu_launches": int(launches),
         "clocks": clk,
     }
