@@ -31,8 +31,8 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # the mixed-precision solve kernel on this workload, from the one-pass ncu
 # capture summarised in profiles/k_solve_mixed_200cubed_dram.md; valid only
 # for the solver source it was taken with (checked by hash, else null).
-TRAFFIC = {"solve_cu_sha1": "df69578ba35d147967c81fadb3c1eb11e4da4b3a",
-           "bytes_per_launch": 835452662528 + 132145155840}
+TRAFFIC = {"solve_cu_sha1": "c1da5bbebc749cbe2eb6fd03fa163deb850c2ef3",
+           "bytes_per_launch": 835378504192 + 132157394176}
 # Iteration counts of this seeded workload (mixed: inner iterations, outer
 # steps), used only to project the CPU oracle's bounded sample to a full solve.
 PROJECTION_ITERS = {"inner": 795, "outer": 5}
@@ -98,6 +98,29 @@ def workload_bytes(n_cells: int, n_faces: int):
     N, F = n_cells, n_faces
     return dict(it64=152 * N + 48 * F, it32=76 * N + 36 * F, amul64=16 * F + 24 * N, amul32=12 * F + 12 * N,
                 resid64=16 * F + 40 * N)
+
+
+def bind_to_gpu_cpus(index: int) -> str:
+    """Restrict this process to the CPUs next to GPU `index` (the GPU's
+    local_cpulist in sysfs), so that pinned host buffers are allocated in the
+    GPU's NUMA node and the end-to-end copies do not cross the CPU link.
+    Returns what was done, for the JSON line."""
+    try:
+        bus = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=pci.bus_id", "--format=csv,noheader"],
+                             capture_output=True, text=True, timeout=30).stdout.strip().lower()
+        dom, rest = bus.split(":", 1)
+        path = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest}/local_cpulist"
+        cpus = set()
+        for part in open(path).read().strip().split(","):
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+        cpus &= os.sched_getaffinity(0)
+        if not cpus:
+            return "unchanged (no local CPU available)"
+        os.sched_setaffinity(0, cpus)
+        return f"{len(cpus)} CPUs local to the GPU"
+    except Exception as e:   # no sysfs entry, no nvidia-smi: keep the inherited affinity
+        return f"unchanged ({type(e).__name__})"
 
 
 class ClockSampler:
@@ -287,6 +310,7 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", init_method="env://")
+    host_affinity = bind_to_gpu_cpus(local)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     import __graft_entry__
@@ -578,7 +602,7 @@ def main():
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "api": "spuma_assemble_laplacian + spuma_pcg_solve with gamma and b copied from pinned host "
                        "memory and x and the solver report copied back, every step",
-                "clocks": clk_e2e},
+                "clocks": clk_e2e, "host_affinity": host_affinity},
         "gpu_launches": int(launches),
         "clocks": clk,
     }

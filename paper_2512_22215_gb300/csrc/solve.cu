@@ -50,26 +50,46 @@ __device__ __forceinline__ Mat<float> mat_of<float>(const SolveArgs& a)
 // Cache priorities.  The matrix streams (entries, row extents, diagonal,
 // rD) are read once per pass: they are loaded evict-first (__ldcs), so that
 // the vectors other rows gather stay in L2; a stand-alone Amul stores its
-// result evict-first too.  FP32 gathers (x in the Amul, w in the sweeps) are
-// loaded evict-last on top of that; FP64 vectors, twice the size, keep the
-// default priority, since pinning them evicts them from each other.
-// Measured at 200^3: stand-alone Amul FP64 168 -> 130 us, FP32 101 -> 91 us;
-// mixed solve 352 -> 333 ms with evict-first streams, 330 ms with the FP32
-// gathers evict-last (FP64 gathers evict-last: Amul 130 -> 146 us).
-template <class T>
+// result evict-first too.  Inside the solver, FP32 gathers (x in the Amul, w
+// in the sweeps) are loaded evict-last on top of that, and the solver hands
+// those lines back (evict-normal) before it returns; FP64 vectors, twice the
+// size, keep the default priority, since pinning them evicts them from each
+// other.  Measured at 200^3: stand-alone Amul FP64 168 -> 130 us, FP32
+// 101 -> 91 us; mixed solve 352 -> 333 ms with evict-first streams, 330 ms
+// with the FP32 gathers evict-last (FP64 gathers evict-last: Amul 130 -> 146 us).
+template <class T, bool KEEP>
 __device__ __forceinline__ unsigned long long keep_policy()
 {
     unsigned long long p = 0;
-    if constexpr (sizeof(T) == 4) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    if constexpr (KEEP && sizeof(T) == 4)
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
+template <bool KEEP>
 __device__ __forceinline__ float gather(const float* v, int c, unsigned long long pol)
 {
-    float r;
-    asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(v + c), "l"(pol) : "memory");
-    return r;
+    if constexpr (KEEP) {
+        float r;
+        asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(v + c), "l"(pol) : "memory");
+        return r;
+    } else {
+        return v[c];
+    }
 }
-__device__ __forceinline__ double gather(const double* v, int c, unsigned long long) { return v[c]; }
+template <bool KEEP>
+__device__ __forceinline__ double gather(const double* v, int c, unsigned long long)
+{
+    return v[c];
+}
+
+// Back to evict-normal: every 128-byte line of [base, base + bytes), spread
+// over the group's threads (a hint; the regions are 256-byte aligned).
+__device__ __forceinline__ void release_lines(const void* base, size_t bytes, int first, int stride)
+{
+    const char* b = static_cast<const char*>(base);
+    for (size_t off = (size_t)first * 128; off < bytes; off += (size_t)stride * 128)
+        asm volatile("applypriority.global.L2::evict_normal [%0], 128;" : : "l"(b + off) : "memory");
+}
 
 // Shapes of the row chains: a row's entries are taken in groups whose column
 // and coefficient loads are issued together, then the gathers, then the FMAs
@@ -107,7 +127,7 @@ template <class T, int R, int G, bool DESC, bool NEG>
 __device__ __forceinline__ void rows_chain(T (&acc)[R], const int (&e0)[R], const int (&e1)[R], const int* col,
                                            const T* coef, const T* vec)
 {
-    const unsigned long long pol = keep_policy<T>();
+    const unsigned long long pol = keep_policy<T, true>();
     for (int off = 0;; off += G) {
         bool more = false;
 #pragma unroll
@@ -127,7 +147,7 @@ __device__ __forceinline__ void rows_chain(T (&acc)[R], const int (&e0)[R], cons
 #pragma unroll
         for (int k = 0; k < R; k++)
 #pragma unroll
-            for (int j = 0; j < G; j++) v[k][j] = c[k][j] >= 0 ? gather(vec, c[k][j], pol) : T(0);
+            for (int j = 0; j < G; j++) v[k][j] = c[k][j] >= 0 ? gather<true>(vec, c[k][j], pol) : T(0);
 #pragma unroll
         for (int k = 0; k < R; k++)
 #pragma unroll
@@ -138,13 +158,14 @@ __device__ __forceinline__ void rows_chain(T (&acc)[R], const int (&e0)[R], cons
 
 // y = A x for R rows: d_p x_p, then the row's lower entries (ascending face)
 // and upper entries (ascending face) taken as one list of nL + nU entries.
-template <class T, int R, int G>
+// KEEP: gathers of x evict-last (inside the solver, FP32).
+template <class T, int R, int G, bool KEEP = true>
 __device__ __forceinline__ void amul_rows(const Mat<T>& A, const T* x, const int (&p)[R], int n, T (&y)[R],
                                           T (&xp)[R])
 {
     if (A.ell_w > 0) {
         // fixed-width layout: no row extents to load, entries coalesced
-        const unsigned long long pol = keep_policy<T>();
+        const unsigned long long pol = keep_policy<T, KEEP>();
 #pragma unroll
         for (int k = 0; k < R; k++) {
             const bool ok = p[k] < n;
@@ -166,7 +187,7 @@ __device__ __forceinline__ void amul_rows(const Mat<T>& A, const T* x, const int
 #pragma unroll
             for (int k = 0; k < R; k++)
 #pragma unroll
-                for (int j = 0; j < G; j++) vv[k][j] = c[k][j] >= 0 ? gather(x, c[k][j], pol) : T(0);
+                for (int j = 0; j < G; j++) vv[k][j] = c[k][j] >= 0 ? gather<KEEP>(x, c[k][j], pol) : T(0);
 #pragma unroll
             for (int k = 0; k < R; k++)
 #pragma unroll
@@ -175,7 +196,7 @@ __device__ __forceinline__ void amul_rows(const Mat<T>& A, const T* x, const int
         }
         return;
     }
-    const unsigned long long pol = keep_policy<T>();
+    const unsigned long long pol = keep_policy<T, KEEP>();
     int l0[R], nl[R], u0[R], nt[R];
 #pragma unroll
     for (int k = 0; k < R; k++) {
@@ -208,7 +229,7 @@ __device__ __forceinline__ void amul_rows(const Mat<T>& A, const T* x, const int
 #pragma unroll
         for (int k = 0; k < R; k++)
 #pragma unroll
-            for (int j = 0; j < G; j++) vv[k][j] = c[k][j] >= 0 ? gather(x, c[k][j], pol) : T(0);
+            for (int j = 0; j < G; j++) vv[k][j] = c[k][j] >= 0 ? gather<KEEP>(x, c[k][j], pol) : T(0);
 #pragma unroll
         for (int k = 0; k < R; k++)
 #pragma unroll
@@ -250,12 +271,11 @@ __device__ __forceinline__ void ell_load(EllRound<T, R, G>& e, const Mat<T>& A, 
 template <class T, int R, int G>
 __device__ __forceinline__ void ell_finish(const EllRound<T, R, G>& e, const Mat<T>& A, const T* x, T (&y)[R])
 {
-    const unsigned long long pol = keep_policy<T>();
     T vv[R][G];
 #pragma unroll
     for (int k = 0; k < R; k++)
 #pragma unroll
-        for (int j = 0; j < G; j++) vv[k][j] = e.c[k][j] >= 0 ? gather(x, e.c[k][j], pol) : T(0);
+        for (int j = 0; j < G; j++) vv[k][j] = e.c[k][j] >= 0 ? gather<false>(x, e.c[k][j], 0) : T(0);
 #pragma unroll
     for (int k = 0; k < R; k++) {
         y[k] = mul_rn(e.d[k], e.xp[k]);
@@ -968,6 +988,9 @@ __device__ bool solve_mixed_reliable(const SolveArgs& a, const Group& g, double 
             pending = true;
         }
     }
+    // the FP32 w and p were gathered evict-last: hand their lines back
+    release_lines(a.wi, 4 * (size_t)a.n, it.first, it.stride);
+    release_lines(a.pi, 4 * (size_t)a.n, it.first, it.stride);
     pf.initial_residual = res0;
     pf.final_residual = res;
     pf.n_iter = n_it;
@@ -1068,6 +1091,8 @@ __device__ bool solve_mixed_restart(const SolveArgs& a, const Group& g, double n
         if (!group_sync(g)) return false;
         outer++;
     }
+    release_lines(a.wi, 4 * (size_t)a.n, it.first, it.stride);
+    release_lines(a.pi, 4 * (size_t)a.n, it.first, it.stride);
     pf.initial_residual = res0;
     pf.final_residual = res;
     pf.n_iter = total;
@@ -1289,7 +1314,7 @@ __global__ void __launch_bounds__(256) k_amul_prepared(int n, Mat<T> A, const T*
         T yy[R], xp[R];
 #pragma unroll
         for (int k = 0; k < R; k++) p[k] = pb + k * stride;
-        amul_rows<T, R, G>(A, x, p, n, yy, xp);
+        amul_rows<T, R, G, false>(A, x, p, n, yy, xp);
 #pragma unroll
         for (int k = 0; k < R; k++)
             if (p[k] < n) __stcs(y + p[k], yy[k]);
