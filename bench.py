@@ -100,6 +100,16 @@ def workload_bytes(n_cells: int, n_faces: int):
                 resid64=16 * F + 40 * N)
 
 
+def parse_cpulist(text: str) -> set:
+    """CPU numbers of a sysfs cpulist ("0-3,8,10-11")."""
+    cpus = set()
+    for part in text.strip().split(","):
+        if part:
+            lo, _, hi = part.partition("-")
+            cpus.update(range(int(lo), int(hi or lo) + 1))
+    return cpus
+
+
 def bind_to_gpu_cpus(index: int) -> str:
     """Restrict this process to the CPUs next to GPU `index` (the GPU's
     local_cpulist in sysfs), so that pinned host buffers are allocated in the
@@ -110,11 +120,7 @@ def bind_to_gpu_cpus(index: int) -> str:
                              capture_output=True, text=True, timeout=30).stdout.strip().lower()
         dom, rest = bus.split(":", 1)
         path = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest}/local_cpulist"
-        cpus = set()
-        for part in open(path).read().strip().split(","):
-            lo, _, hi = part.partition("-")
-            cpus.update(range(int(lo), int(hi or lo) + 1))
-        cpus &= os.sched_getaffinity(0)
+        cpus = parse_cpulist(open(path).read()) & os.sched_getaffinity(0)
         if not cpus:
             return "unchanged (no local CPU available)"
         os.sched_setaffinity(0, cpus)

@@ -63,3 +63,11 @@ def test_workload_bytes_formulas():
     assert w["amul64"] == 16 * 23_880_000 + 24 * 8_000_000          # 574.08 MB
     assert w["it64"] == 152 * 8_000_000 + 48 * 23_880_000
     assert w["it32"] == 76 * 8_000_000 + 36 * 23_880_000
+
+
+def test_cpulist_parsing():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench.parse_cpulist("5") == {5}
+    assert bench.parse_cpulist("") == set()
