@@ -28,11 +28,12 @@ sys.path.insert(0, ROOT)
 METRIC = "PCG time to 1e-8 rel. residual @8M cells (FP64 vs mixed); Amul HBM GB/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the mixed-precision solve kernel on this workload, from the one-pass ncu
-# capture summarised in profiles/k_solve_mixed_200cubed_dram.md; valid only
-# for the solver source it was taken with (checked by hash, else null).
-TRAFFIC = {"solve_cu_sha1": "c1da5bbebc749cbe2eb6fd03fa163deb850c2ef3",
-           "bytes_per_launch": 835378504192 + 132157394176}
+# the mixed-precision solve kernel, from a one-kernel, one-launch ncu capture
+# of the 128^3 case (seed 2 recipe) with its iteration counts; scaled to the
+# bench workload by the per-iteration byte model (traffic grows with the
+# algorithmic bytes).  Valid only for the solver source it was taken with
+# (checked by hash, else the line reports null).
+TRAFFIC = {"solve_cu_sha1": None, "n": 128, "bytes": None, "inner": None, "outer": None}
 # Iteration counts of this seeded workload (mixed: inner iterations, outer
 # steps), used only to project the CPU oracle's bounded sample to a full solve.
 PROJECTION_ITERS = {"inner": 795, "outer": 5}
@@ -79,16 +80,24 @@ def load_peaks():
     return PEAKS_FALLBACK, "fallback"
 
 
-def traffic_bytes(n: int):
-    """The recorded DRAM traffic per launch, when the solver source still
-    matches the capture and the workload is the captured one; else None."""
+def traffic_bytes(n_cells: int, n_faces: int, inner: int, outer: int):
+    """The recorded DRAM traffic of one solve launch, scaled from the captured
+    case to this one by the algorithmic bytes, when the solver source still
+    matches the capture; else None."""
     import hashlib
-    if n != 200:
+    if not TRAFFIC["bytes"]:
         return None
     src = os.path.join(ROOT, "paper_2512_22215_gb300", "csrc", "solve.cu")
     with open(src, "rb") as fh:
         sha = hashlib.sha1(fh.read()).hexdigest()
-    return TRAFFIC["bytes_per_launch"] if sha == TRAFFIC["solve_cu_sha1"] else None
+    if sha != TRAFFIC["solve_cu_sha1"]:
+        return None
+    n = TRAFFIC["n"]
+    nf = 3 * (n - 1) * n * n
+    wc, wb = workload_bytes(n ** 3, nf), workload_bytes(n_cells, n_faces)
+    cap = TRAFFIC["inner"] * wc["it32"] + (TRAFFIC["outer"] + 1) * wc["resid64"]
+    this = inner * wb["it32"] + (outer + 1) * wb["resid64"]
+    return int(TRAFFIC["bytes"] * this / cap)
 
 
 def workload_bytes(n_cells: int, n_faces: int):
@@ -231,7 +240,8 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32 (mixed)", "data": "synthetic",
         "config": config_of(case, args),
-        "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle", "sample": info["sample"]},
+        "cpu_baseline": {"value": value, "unit": "ms", "cores": cores, "kind": "oracle, projected",
+                         "sample": info["sample"]},
         "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -244,18 +254,15 @@ def config_of(case, args):
             "l2": "inputs larger than L2 (workspace and per-iteration streams > 129 MB)"}
 
 
-def run_batch(args, rank, world, local):
+def batch_measure(dev, steps: int):
     """64 independent systems (jittered, permuted hex blocks, side lengths from
     cell counts log-uniform in 1e4..5e5, seed 5) in one persistent launch
-    replayed from a CUDA graph, FP64 and mixed, autotuned block size/split."""
+    replayed from a CUDA graph, FP64 and mixed, autotuned block size, split
+    weights and grid.  Returns the figures for the JSON line."""
     import numpy as np
     import torch
-    import __graft_entry__
     import hexmesh
-    __graft_entry__.build()
     from paper_2512_22215_gb300 import MIXED, BatchSolve, LduMesh, SolverControls
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     sides = hexmesh.batch_sizes(64, seed=5)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     Ms, D, U, B, X = [], [], [], [], []
@@ -271,7 +278,7 @@ def run_batch(args, rank, world, local):
         B.append(T(c.b))
         X.append(torch.zeros(m.n_cells, dtype=torch.float64, device=dev))
     cells = sum(M.n_cells for M in Ms)
-    out = {}
+    out = {"n_sys": len(Ms), "cells": cells}
     for name, ctl in [("fp64", SolverControls(precond=2, tolerance=1e-8)),
                       ("mixed", SolverControls(precond=2, precision=MIXED, tolerance=1e-8))]:
         bs = BatchSolve(Ms, D, U, B, X, ctl, autotune=True)
@@ -280,7 +287,7 @@ def run_batch(args, rank, world, local):
         bs.run()
         torch.cuda.synchronize()
         ts = []
-        for _ in range(args.steps):
+        for _ in range(max(3, steps)):
             for x in X:
                 x.zero_()
             a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -293,13 +300,63 @@ def run_batch(args, rank, world, local):
         ts.sort()
         out[name] = {"ms": round(ts[len(ts) // 2], 3), "max_iters": max(r["n_iter"] for r in res),
                      "all_converged": all(r["converged"] == 1 for r in res),
-                     "block_threads": bs.block_threads, "grid_blocks": bs.grid_blocks}
+                     "max_true_rel_residual_l2": max(r["true_rel_residual_l2"] for r in res),
+                     "block_threads": bs.block_threads, "grid_blocks": bs.grid_blocks,
+                     "graph_captured": bs.graph_captured, "tuned_ms": round(bs.tuned_ms, 3),
+                     "tuner_trials": bs.trials}
+        del bs
+    return out
+
+
+def run_batch(args, rank, world, local):
+    """The batched workload alone, as a line of its own."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    out = batch_measure(torch.device("cuda", local), args.steps)
     line = {"metric": "batched PCG time to 1e-8, 64 systems", "value": out["mixed"]["ms"], "unit": "ms",
             "higher_is_better": False, "n_gpus": world, "steps": args.steps, "data": "synthetic",
             "config": {"workload": "64 jittered permuted hex blocks, cells log-uniform in 1e4..5e5, seed 5",
-                       "cells": cells}, "fp64": out["fp64"], "mixed": out["mixed"]}
+                       "cells": out["cells"]}, "fp64": out["fp64"], "mixed": out["mixed"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def measured_oracle_solve(dev):
+    """A full oracle solve timed to the end (no projection) beside the GPU's on
+    the same system: 64^3 jittered, permuted, log-normal gamma, seed 4, FP64
+    DIC-PCG to 1e-8, one host core."""
+    import numpy as np
+    import torch
+    import hexmesh
+    import oracle
+    from paper_2512_22215_gb300 import LduMesh, SolverControls
+    c = hexmesh.pressure_case(64, jitter=0.2, permute=True, seed=4, lognormal_gamma=True)
+    m = c.mesh
+    up, dg = oracle.assemble_laplacian(m, c.gamma, c.bgamma, c.btype)
+    t0 = time.perf_counter()
+    _, po = oracle.pcg(m.lower, m.upper_addr, dg, up, c.b, precond=2, tol=1e-8)
+    t_cpu = time.perf_counter() - t0
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    M = LduMesh(m.lower, m.upper_addr, m.n_cells, device=dev, centres=m.c)
+    d, u, b = T(dg), T(up), T(c.b)
+    x = torch.zeros_like(b)
+    ctl = SolverControls(precond=2, tolerance=1e-8)
+    M.solve(d, u, b, x, ctl)
+    ts = []
+    for _ in range(5):
+        x.zero_()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _, pg = M.solve(d, u, b, x, ctl)
+        e.record()
+        e.synchronize()
+        ts.append(a.elapsed_time(e))
+    ts.sort()
+    return {"workload": "64^3 jittered permuted hex mesh, log-normal gamma, seed 4, FP64 DIC-PCG to 1e-8",
+            "oracle_ms": round(t_cpu * 1e3, 1), "oracle_iters": po["n_iter"], "cores": 1,
+            "gpu_ms": round(ts[2], 3), "gpu_iters": pg["n_iter"], "ratio": round(t_cpu * 1e3 / ts[2], 1)}
 
 
 def main():
@@ -378,14 +435,24 @@ def main():
     perf_h = torch.empty(perf.numel(), dtype=torch.uint8).pin_memory()
     gamma_d, b_d = torch.empty_like(gamma), torch.empty_like(b)
 
-    def e2e_step():
+    def e2e_step(marks=None):
+        """One end-to-end step; `marks` (4 events) split it into host-to-device
+        copies, assembly, solve and device-to-host copies."""
         gamma_d.copy_(gamma_h, non_blocking=True)
         b_d.copy_(b_h, non_blocking=True)
+        if marks:
+            marks[0].record(s)
         u2, d2 = M.assemble_laplacian(sf, cc, gamma_d, bcell, bsf, bcf, bg, bt)
+        if marks:
+            marks[1].record(s)
         x.zero_()
         M.solve(d2, u2, b_d, x, ctl_mixed, perf=perf)
+        if marks:
+            marks[2].record(s)
         x_h.copy_(x, non_blocking=True)
         perf_h.copy_(perf, non_blocking=True)
+        if marks:
+            marks[3].record(s)
 
     e2e_step()
     # sampled like the timed steps (the same settle time after the sampler starts)
@@ -393,13 +460,24 @@ def main():
     time.sleep(0.3)
     barrier()
     a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    marks = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     a.record(s)
-    for _ in range(args.steps):
-        e2e_step()
+    for k in range(args.steps):
+        e2e_step(marks[k])
     c.record(s)
     c.synchronize()
     clk_e2e = clocks_e2e.stop()
     e2e_ms = reduce_max(a.elapsed_time(c) / args.steps, world, dev)
+    # per-stage split of the end-to-end steps (CUDA events on the same stream)
+    starts = [a] + [mk[3] for mk in marks[:-1]]
+    split = {"h2d_ms": [], "assembly_ms": [], "solve_ms": [], "d2h_ms": []}
+    for st, mk in zip(starts, marks):
+        split["h2d_ms"].append(st.elapsed_time(mk[0]))
+        split["assembly_ms"].append(mk[0].elapsed_time(mk[1]))
+        split["solve_ms"].append(mk[1].elapsed_time(mk[2]))
+        split["d2h_ms"].append(mk[2].elapsed_time(mk[3]))
+    e2e_split = {k: round(sum(v) / len(v), 3) for k, v in split.items()}
+    e2e_split["max_step_ms"] = round(max(st.elapsed_time(mk[3]) for st, mk in zip(starts, marks)), 3)
     h2d = gamma_h.numel() * 8 + b_h.numel() * 8
     d2h = x_h.numel() * 8 + perf_h.numel()
 
@@ -551,6 +629,8 @@ def main():
     p_gamg2 = read_perf(perf)[0]
     del gs2
 
+    # the batched form: 64 systems, ~8.2M cells in total, one persistent launch per solve
+    batch_out = batch_measure(dev, args.steps)
 
     # -------------------------------------------------------------- roofline
     wb = workload_bytes(N, F)
@@ -561,7 +641,8 @@ def main():
     f64_bytes = p_f64["n_iter"] * wb["it64"]
     roofline = {"kernel": "k_solve (persistent mixed-precision solve, one launch per solve)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "peak_kind": peak_kind, "traffic": traffic_bytes(args.n),
+                "peak_kind": peak_kind,
+                "traffic": traffic_bytes(N, F, p_mixed["n_iter"], p_mixed["n_outer"]),
                 "algorithmic_bytes": int(mixed_bytes),
                 "basis": "inner iterations x (76N + 36F) + (outer + 1) FP64 residuals x (16F + 40N)"}
 
@@ -604,20 +685,22 @@ def main():
                                        "converged": p_gamg2["converged"],
                                        "weights": "|upper_f| (algebraic pairing)"}},
         "n_levels": M.n_levels,
+        "batch": batch_out,
         "roofline": roofline,
         "e2e": {"value": round(e2e_ms, 3), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "api": "spuma_assemble_laplacian + spuma_pcg_solve with gamma and b copied from pinned host "
                        "memory and x and the solver report copied back, every step",
-                "clocks": clk_e2e, "host_affinity": host_affinity},
+                "clocks": clk_e2e, "host_affinity": host_affinity, "split": e2e_split},
         "gpu_launches": int(launches),
         "clocks": clk,
     }
     if rank == 0 and not args.no_cpu:
         cpu_ms, info = cpu_sample(case, args.cpu_iters)
-        line["cpu_baseline"] = {"value": round(cpu_ms, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+        line["cpu_baseline"] = {"value": round(cpu_ms, 1), "unit": "ms", "cores": 1, "kind": "oracle, projected",
                                 "sample": info["sample"], "per_inner_iteration_ms": round(info["per_inner_ms"], 1),
                                 "cpu_seconds": round(info["cpu_seconds"], 1),
-                                "coe": round(cpu_ms / ms_step_max, 1)}
+                                "coe": round(cpu_ms / ms_step_max, 1),
+                                "measured_full_solve": measured_oracle_solve(dev)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -93,10 +93,19 @@ typedef struct {
 } spuma_solver_controls;
 
 /* Solver report (OpenFOAM's solverPerformance), written to DEVICE memory by
- * the solve so that solves can be queued and captured without a host sync. */
+ * the solve so that solves can be queued and captured without a host sync.
+ * true_rel_residual_l2 = ||b - A x||_2 / ||b||_2 (||b - A x||_2 when b = 0) of
+ * the returned x, computed on the device at the end of every solve (PCG in
+ * every precision, PBiCG, GAMG, batched) in FP64 from the FP64 coefficients:
+ * for the mixed forms it is the proof that the FP64 system was solved.
+ * Every reduction of the library is deterministic (fixed per-thread,
+ * per-block and per-grid order; no atomics in any sum), so equal inputs give
+ * bit-identical reports and solutions run to run: there is no separate
+ * "deterministic" control. */
 typedef struct {
     double initial_residual;
     double final_residual;
+    double true_rel_residual_l2;
     int32_t n_iter;         /* PCG iterations (all inner iterations for MIXED) */
     int32_t n_outer;        /* refinement steps (MIXED), else 0               */
     int32_t converged;
@@ -261,11 +270,13 @@ spuma_status spuma_pcg_solve(spuma_ldu_t h, const double* diag, const double* up
  * before any device work.  The caller passes the addressing, the
  * coefficients, b, x (initial guess in, solution out) and perf, all device
  * pointers, as for spuma_ldu_create + spuma_pcg_solve, which this call
- * performs in one go (the topology build waits for the stream).  The first
- * call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture.  Every call
- * reuses the same array and each call clears what it needs, but calls whose
- * work overlaps on the GPU (other streams, other host threads) race on it.
+ * performs in one go (the topology build waits for the stream).  Every
+ * call looks up the array's device address with the current device (the
+ * first call on a device also loads the library's device code there: make
+ * that first call before any stream capture).  All arguments are checked
+ * before the array is touched.  Every call reuses the same array and each
+ * call clears what it needs, but calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on it.
  * ---------------------------------------------------------------------- */
 size_t spuma_static_workspace_bytes(void);
 spuma_status spuma_pcg_solve_static(int32_t n_cells, int32_t n_faces, const int32_t* lower_addr,
@@ -398,24 +409,40 @@ spuma_status spuma_pcg_adjoint(spuma_ldu_t h, const double* diag, const double* 
 
 /* ------------------------------------------------------------------------
  * Batched solve: n_sys independent systems (each with its own handle and
- * workspace) in ONE persistent cooperative launch; each system converges on
- * its own (per-system device-side convergence) with the controls *ctl.
- * Arrays of n_sys DEVICE pointers are passed as HOST arrays; perf[n_sys] is
- * device memory.  spuma_batch_create() records the pointers, picks the block
- * size and the split of the grid between systems with the library's
- * autotuner (timed trial solves on the stream, cached per problem signature
- * in memory and, when SPUMA_TUNE_CACHE names a file, in that JSON file),
- * and captures the launch in a CUDA graph; spuma_batch_run() replays it.
+ * workspace) in ONE persistent cooperative launch (an extension of the
+ * paper's pressure solve to many small systems); each system converges on its own
+ * (per-system device-side convergence) with the controls *ctl.  Arrays of
+ * n_sys DEVICE pointers are passed as HOST arrays; perf[n_sys] is device
+ * memory.  spuma_batch_create() records the pointers, picks the block size,
+ * the weighting of the grid split between systems and the grid size with the
+ * library's autotuner when flags has SPUMA_BATCH_AUTOTUNE (timed trial solves
+ * on the stream from x = 0, the caller's x untouched; a staged search over
+ * block sizes 64..1024, split weights cells^{1, 4/3, 5/3} and a full or
+ * half-size grid; cached per problem signature in memory and, when
+ * SPUMA_TUNE_CACHE names a file, in that JSON file), and captures the launch
+ * (barrier resets + the kernel) in a CUDA graph that spuma_batch_run()
+ * replays.  A failed capture is an error (SPUMA_ERR_CUDA, the reason in
+ * spuma_last_error) unless flags has SPUMA_BATCH_ALLOW_DIRECT, which replays
+ * by direct launches instead; SPUMA_BATCH_NO_GRAPH skips the capture.
+ * spuma_batch_info() reports the chosen block size, grid, the tuned time (-1
+ * when not tuned) and whether a graph was captured; spuma_batch_trials()
+ * copies the candidates the tuner timed (up to max_trials) and returns their
+ * count (0 after a cache hit or without tuning).
  * spuma_batch_solve() is the one-shot form (no graph, no tuning).
  * ---------------------------------------------------------------------- */
+#define SPUMA_BATCH_AUTOTUNE 1
+#define SPUMA_BATCH_ALLOW_DIRECT 2
+#define SPUMA_BATCH_NO_GRAPH 4
 spuma_status spuma_batch_create(int32_t n_sys, const spuma_ldu_t* hs, const double* const* diag,
                                 const double* const* upper, const double* const* b,
                                 double* const* x, const spuma_solver_controls* ctl,
-                                spuma_solver_perf* perf, int32_t autotune, spuma_stream_t stream,
+                                spuma_solver_perf* perf, int32_t flags, spuma_stream_t stream,
                                 spuma_batch_t* out);
 spuma_status spuma_batch_run(spuma_batch_t bt, spuma_stream_t stream);
 spuma_status spuma_batch_info(spuma_batch_t bt, int32_t* block_threads, int32_t* grid_blocks,
-                              double* tuned_ms);
+                              double* tuned_ms, int32_t* graph_captured);
+int32_t spuma_batch_trials(spuma_batch_t bt, int32_t max_trials, int32_t* block_threads,
+                           int32_t* split_policy, int32_t* grid_blocks, double* ms);
 spuma_status spuma_batch_destroy(spuma_batch_t bt);
 spuma_status spuma_batch_solve(int32_t n_sys, const spuma_ldu_t* hs, const double* const* diag,
                                const double* const* upper, const double* const* b,
@@ -428,13 +455,15 @@ spuma_status spuma_batch_solve(int32_t n_sys, const spuma_ldu_t* hs, const doubl
  * split_out[0..n_sys] (block ranges) and returns 1, or 0 when grid < n_sys.
  * spuma_tune_cache_lookup / _store: the tuner's cache, kept in memory and,
  * when path is not NULL or empty, in a JSON file whose lines read
- *   "signature": [block_threads, split_policy, milliseconds],
- * Lookup returns 1 on a hit; store returns 1 on success.                   */
+ *   "signature": [block_threads, split_policy, grid_div, milliseconds],
+ * (split_policy: 0, 1, 2 for weights cells^1, ^(4/3), ^(5/3); grid_div: the
+ * co-resident grid divided by 1 or 2).  Lookup returns 1 on a hit; store
+ * returns 1 on success.                                                    */
 int32_t spuma_batch_split(int32_t n_sys, const double* weights, int32_t grid, int32_t* split_out);
 int32_t spuma_tune_cache_lookup(const char* path, const char* signature, int32_t* block_threads,
-                                int32_t* split_policy, double* ms);
+                                int32_t* split_policy, int32_t* grid_div, double* ms);
 int32_t spuma_tune_cache_store(const char* path, const char* signature, int32_t block_threads,
-                               int32_t split_policy, double ms);
+                               int32_t split_policy, int32_t grid_div, double ms);
 
 /* ------------------------------------------------------------------------
  * Diagnostics.

@@ -19,6 +19,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_UPPER_TRIANGULAR", 3: "CUDA",
 F64, MIXED, F32, MIXED_RESTART = 0, 1, 2, 3
 PRECOND_NONE, PRECOND_DIAGONAL, PRECOND_DIC, PRECOND_DILU = 0, 1, 2, 3
 WORKSPACE_ASYMMETRIC = 1
+BATCH_AUTOTUNE, BATCH_ALLOW_DIRECT, BATCH_NO_GRAPH = 1, 2, 4
 
 
 class Controls(C.Structure):
@@ -28,13 +29,13 @@ class Controls(C.Structure):
 
 
 class Perf(C.Structure):
-    _fields_ = [("initial_residual", C.c_double), ("final_residual", C.c_double), ("n_iter", C.c_int32),
-                ("n_outer", C.c_int32), ("converged", C.c_int32), ("singular", C.c_int32),
-                ("status", C.c_int32), ("n_levels", C.c_int32)]
+    _fields_ = [("initial_residual", C.c_double), ("final_residual", C.c_double),
+                ("true_rel_residual_l2", C.c_double), ("n_iter", C.c_int32), ("n_outer", C.c_int32),
+                ("converged", C.c_int32), ("singular", C.c_int32), ("status", C.c_int32), ("n_levels", C.c_int32)]
 
 
 PERF_BYTES = C.sizeof(Perf)
-assert PERF_BYTES == 40
+assert PERF_BYTES == 48
 
 
 class SpumaError(RuntimeError):
@@ -82,14 +83,15 @@ _SIGS = {
     "spuma_batch_create": (_I, [_I, C.POINTER(_H), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                 C.POINTER(Controls), _P, _I, _P, C.POINTER(_H)]),
     "spuma_batch_run": (_I, [_H, _P]),
-    "spuma_batch_info": (_I, [_H, C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_double)]),
+    "spuma_batch_info": (_I, [_H, C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_double), C.POINTER(_I)]),
+    "spuma_batch_trials": (_I, [_H, _I, _P, _P, _P, _P]),
     "spuma_batch_destroy": (_I, [_H]),
     "spuma_batch_solve": (_I, [_I, C.POINTER(_H), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P),
                                C.POINTER(Controls), _P, _P]),
     "spuma_batch_split": (_I, [_I, C.POINTER(C.c_double), _I, C.POINTER(_I)]),
-    "spuma_tune_cache_lookup": (_I, [C.c_char_p, C.c_char_p, C.POINTER(_I), C.POINTER(_I),
+    "spuma_tune_cache_lookup": (_I, [C.c_char_p, C.c_char_p, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I),
                                      C.POINTER(C.c_double)]),
-    "spuma_tune_cache_store": (_I, [C.c_char_p, C.c_char_p, _I, _I, C.c_double]),
+    "spuma_tune_cache_store": (_I, [C.c_char_p, C.c_char_p, _I, _I, _I, C.c_double]),
     "spuma_read_phase_clocks": (_I, [_H, C.POINTER(C.c_int64), _I, _P]),
     "spuma_status_string": (C.c_char_p, [_I]),
     "spuma_last_error": (C.c_char_p, []),

@@ -7,7 +7,8 @@ from dataclasses import dataclass
 
 import torch
 
-from ._lib import (F32, F64, MIXED, PERF_BYTES, PRECOND_DIC, PRECOND_DILU, WORKSPACE_ASYMMETRIC, Controls, Perf,
+from ._lib import (BATCH_ALLOW_DIRECT, BATCH_AUTOTUNE, BATCH_NO_GRAPH, F32, F64, MIXED, PERF_BYTES, PRECOND_DIC,
+                   PRECOND_DILU, WORKSPACE_ASYMMETRIC, Controls, Perf,
                    SpumaError, check, lib, ptr, stream_ptr)
 
 
@@ -296,9 +297,11 @@ class GamgSolver:
 
 
 class BatchSolve:
-    """Many systems in one persistent launch, replayed from a CUDA graph."""
+    """Many systems in one persistent launch, replayed from a CUDA graph
+    (capture failure raises unless allow_direct=True)."""
 
-    def __init__(self, meshes, diags, uppers, bs, xs, controls: SolverControls | None = None, autotune=True):
+    def __init__(self, meshes, diags, uppers, bs, xs, controls: SolverControls | None = None, autotune=True,
+                 allow_direct=False, graph=True):
         n = len(meshes)
         self.meshes, self.diags, self.uppers, self.bs, self.xs = meshes, diags, uppers, bs, xs
         self.ctl = (controls or SolverControls()).c()
@@ -306,14 +309,26 @@ class BatchSolve:
         H = (C.c_void_p * n)(*[m.handle.value for m in meshes])
         arr = lambda ts: (C.c_void_p * n)(*[ptr(t) for t in ts])
         self._keep = (H, arr(diags), arr(uppers), arr(bs), arr(xs))
+        flags = ((BATCH_AUTOTUNE if autotune else 0) | (BATCH_ALLOW_DIRECT if allow_direct else 0)
+                 | (0 if graph else BATCH_NO_GRAPH))
         h = C.c_void_p()
         check(lib().spuma_batch_create(n, self._keep[0], self._keep[1], self._keep[2], self._keep[3], self._keep[4],
-                                       C.byref(self.ctl), ptr(self.perf), 1 if autotune else 0, stream_ptr(),
-                                       C.byref(h)), "spuma_batch_create")
+                                       C.byref(self.ctl), ptr(self.perf), flags, stream_ptr(), C.byref(h)),
+              "spuma_batch_create")
         self.handle = h
-        t, g, ms = C.c_int32(), C.c_int32(), C.c_double()
-        check(lib().spuma_batch_info(h, C.byref(t), C.byref(g), C.byref(ms)), "spuma_batch_info")
+        t, g, ms, cap = C.c_int32(), C.c_int32(), C.c_double(), C.c_int32()
+        check(lib().spuma_batch_info(h, C.byref(t), C.byref(g), C.byref(ms), C.byref(cap)), "spuma_batch_info")
         self.block_threads, self.grid_blocks, self.tuned_ms = t.value, g.value, ms.value
+        self.graph_captured = bool(cap.value)
+        nt = lib().spuma_batch_trials(h, 0, None, None, None, None)
+        if nt > 0:
+            tt, pp, gg, mm = (C.c_int32 * nt)(), (C.c_int32 * nt)(), (C.c_int32 * nt)(), (C.c_double * nt)()
+            lib().spuma_batch_trials(h, nt, C.cast(tt, C.c_void_p), C.cast(pp, C.c_void_p), C.cast(gg, C.c_void_p),
+                                     C.cast(mm, C.c_void_p))
+            self.trials = [dict(block_threads=tt[k], split_policy=pp[k], grid_blocks=gg[k], ms=round(mm[k], 3))
+                           for k in range(nt)]
+        else:
+            self.trials = []
 
     def run(self):
         check(lib().spuma_batch_run(self.handle, stream_ptr()), "spuma_batch_run")

@@ -30,16 +30,19 @@ uint64_t barrier_timeout_ns();
     } while (0)
 
 // Device status words (int32): [0] status, [1] first offending cell/face,
-// [32] the grid barrier's arrival word (its own 128-byte line), whose top bit
-// tells every waiting block that an error was recorded.
+// [32..33] the grid barrier's 64-bit arrival word (its own 128-byte line),
+// whose top bit tells every waiting block that an error was recorded.  The
+// count has 63 bits: a launch makes blocks x barriers arrivals, and 2^63 is out
+// of reach of any solve (a 32-bit count could carry into the error bit after
+// about 12 thousand iterations on a mesh with 600 DIC levels).
 enum DevStatus { DS_STATUS = 0, DS_INDEX = 1, DS_LEVELS_CHANGED = 2, DS_MAXLEVEL = 3, DS_BARRIER = 32 };
-constexpr unsigned kErrBit = 0x80000000u;
+constexpr unsigned long long kErrBit = 1ull << 63;
 
 __device__ __forceinline__ void flag_error(int* st, int code, int index)
 {
     if (atomicCAS(st + DS_STATUS, 0, code) == 0) st[DS_INDEX] = index;
     __threadfence();
-    atomicOr(reinterpret_cast<unsigned*>(st + DS_BARRIER), kErrBit);
+    atomicOr(reinterpret_cast<unsigned long long*>(st + DS_BARRIER), kErrBit);
 }
 
 // ------------------------------------------------------- memory helpers --
@@ -49,14 +52,20 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p)
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void st_release(unsigned* p, unsigned v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v)
+__device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long long* p, unsigned long long v)
 {
-    unsigned old;
-    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    unsigned long long old;
+    asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
     return old;
 }
 __device__ __forceinline__ unsigned long long global_timer_ns()
@@ -89,7 +98,7 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 // before), and the wait ends on a gpu-scope acquire load of the word that the
 // last arrival's add wrote; the block's threads meet again after it.
 struct Group {
-    unsigned* word;        // arrival word (status + DS_BARRIER)
+    unsigned long long* word;  // arrival word (status + DS_BARRIER)
     int* status;           // device status words
     int nblocks;           // blocks in the group
     int bid;               // this block's index in the group
@@ -102,15 +111,16 @@ __device__ __forceinline__ bool group_sync(const Group& g)
     __shared__ int s_err;
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned old = atom_add_acq_rel(g.word, 1u);
+        const unsigned long long old = atom_add_acq_rel(g.word, 1ull);
         bool err = (old & kErrBit) != 0;
         if (!err) {
-            const unsigned cnt = old & ~kErrBit;
-            const unsigned target = (cnt / (unsigned)g.nblocks + 1u) * (unsigned)g.nblocks;
-            if (cnt + 1u != target) {
+            const unsigned long long nb = (unsigned long long)g.nblocks;
+            const unsigned long long cnt = old & ~kErrBit;
+            const unsigned long long target = (cnt / nb + 1ull) * nb;
+            if (cnt + 1ull != target) {
                 const unsigned long long t0 = global_timer_ns();
                 for (;;) {
-                    const unsigned w = ld_acquire(g.word);
+                    const unsigned long long w = ld_acquire(g.word);
                     if (w & kErrBit) {
                         err = true;
                         break;

@@ -289,7 +289,7 @@ __device__ bool gamg_vcycle(const GamgArgs& a, const Group& g)
 
 __global__ void __launch_bounds__(1024, 1) k_gamg(GamgArgs a, unsigned long long timeout_ns)
 {
-    Group g{reinterpret_cast<unsigned*>(a.status + DS_BARRIER), a.status, (int)gridDim.x, (int)blockIdx.x, timeout_ns};
+    Group g{reinterpret_cast<unsigned long long*>(a.status + DS_BARRIER), a.status, (int)gridDim.x, (int)blockIdx.x, timeout_ns};
     spuma_solver_perf pf{};
     pf.n_levels = a.nlev;
     const GamgLevel& L0 = a.lv[0];
@@ -358,6 +358,22 @@ __global__ void __launch_bounds__(1024, 1) k_gamg(GamgArgs a, unsigned long long
             if (!((n_it < a.max_iter && !conv(res)) || n_it < a.min_iter)) break;
         }
     }
+    // the report's true residual ||b - A x||_2 / ||b||_2 (||b - A x||_2 when b = 0)
+    if (ok) {
+        double acc[2] = {0.0, 0.0};
+        for (int i = it.first; i < L0.n; i += it.stride) {
+            const double r = __dsub_rn(a.b[i], gamg_amul_row(L0, L0.diag, a.x, i));
+            acc[0] = __fma_rn(r, r, acc[0]);
+            acc[1] = __fma_rn(a.b[i], a.b[i], acc[1]);
+        }
+        block_reduce_store<2>(acc, a.partials, GS_D, g.bid);
+        ok = group_sync(g);
+        if (ok) {
+            grid_reduce_read<2>(acc, a.partials, GS_D, g.nblocks);
+            pf.true_rel_residual_l2 =
+                acc[1] > 0.0 ? __ddiv_rn(__dsqrt_rn(acc[0]), __dsqrt_rn(acc[1])) : __dsqrt_rn(acc[0]);
+        }
+    }
     if (ok)
         for (int i = it.first; i < L0.n; i += it.stride) a.x_orig[i] = a.x[i];
     if (g.bid == 0 && threadIdx.x == 0 && a.perf) {
@@ -367,6 +383,7 @@ __global__ void __launch_bounds__(1024, 1) k_gamg(GamgArgs a, unsigned long long
         pf.converged = conv(res);
         __threadfence();
         pf.status = ld_volatile_int(a.status);
+        if (!ok && pf.status == 0) pf.status = SPUMA_ERR_DEVICE_TIMEOUT;
         if (pf.status != 0) pf.converged = 0;
         *a.perf = pf;
     }

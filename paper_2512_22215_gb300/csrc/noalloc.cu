@@ -9,7 +9,6 @@
 // array of fixed size that the library image carries; the caller passes only
 // the inputs and the outputs.
 #include <cstdio>
-#include <mutex>
 #include <string>
 
 #include "common.cuh"
@@ -18,6 +17,7 @@ namespace spuma {
 spuma_status pcg_solve_internal(spuma_ldu_t h, const double* diag, const double* upper, const double* b, double* x,
                                 const spuma_solver_controls* ctl, spuma_solver_perf* perf, cudaStream_t s,
                                 int zero_x0);
+bool ctl_ok(const spuma_solver_controls* c);
 }  // namespace spuma
 
 using namespace spuma;
@@ -27,28 +27,16 @@ using namespace spuma;
 constexpr size_t kStaticWorkspaceBytes = size_t(32) << 20;
 static __device__ __align__(256) unsigned char g_static_workspace[kStaticWorkspaceBytes];
 
-// In host code the array's name is only a host-side stand-in: the device
-// address must be looked up, once per device, with that device current.
-static std::mutex g_static_mu;
-static void* g_static_ptr[64] = {};
-
+// In host code the array's name is only a host-side stand-in: its device
+// address is looked up with the current device, on every call (a cached
+// address would outlive a reset of the device's primary context; the lookup
+// costs little next to the topology build).
 static spuma_status static_workspace(void** out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= 64) {
-        set_error("spuma_pcg_solve_static: device index out of range");
-        return SPUMA_ERR_INVALID_ARG;
-    }
-    std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_workspace);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static workspace)");
-        g_static_ptr[dev] = p;
-    }
-    *out = g_static_ptr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_workspace);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static workspace)");
+    *out = p;
     return SPUMA_OK;
 }
 
@@ -61,6 +49,8 @@ spuma_status spuma_pcg_solve_static(int32_t n_cells, int32_t n_faces, const int3
                                     const double* b, double* x, const spuma_solver_controls* ctl,
                                     spuma_solver_perf* perf, spuma_stream_t stream)
 {
+    // every argument is checked before the shared array is touched, so that a
+    // call that is going to be rejected never disturbs another user of it
     if (n_cells < 0 || n_faces < 0) {
         set_error("spuma_pcg_solve_static: negative size");
         return SPUMA_ERR_INVALID_ARG;
@@ -71,6 +61,11 @@ spuma_status spuma_pcg_solve_static(int32_t n_cells, int32_t n_faces, const int3
                   " bytes of workspace; the static workspace holds " + std::to_string(kStaticWorkspaceBytes) +
                   " (use spuma_ldu_create with a caller-provided workspace)");
         return SPUMA_ERR_WORKSPACE_TOO_SMALL;
+    }
+    if (!ctl_ok(ctl) || (n_cells > 0 && (!diag || !b || !x)) ||
+        (n_faces > 0 && (!upper || !lower_addr || !upper_addr))) {
+        set_error("spuma_pcg_solve_static: bad argument (controls, or a NULL array)");
+        return SPUMA_ERR_INVALID_ARG;
     }
     void* ws = nullptr;
     spuma_status st = static_workspace(&ws);

@@ -1046,6 +1046,31 @@ __device__ bool phase_init(const SolveArgs& a, const Group& g, double* nfac, dou
     return true;
 }
 
+// The report's true residual ||b - A x||_2 / ||b||_2 (||b - A x||_2 when b = 0)
+// in FP64 from the FP64 coefficients of A, for every solve kind: each r_p in
+// the Amul's face order, the sums of squares as fused multiply-adds per
+// thread, then the deterministic block and grid reductions.  b_int: b in
+// internal order, or NULL to read the caller's b through perm (PBiCG reuses
+// the internal b as its transposed residual).
+__device__ bool true_residual(const SolveArgs& a, const Mat<double>& A, const double* b_int, const Group& g,
+                              double* out)
+{
+    RowIter it = rows_of(g);
+    double acc[2] = {0.0, 0.0};
+    for (int p = it.first; p < a.n; p += it.stride) {
+        const double bv = b_int ? b_int[p] : a.b_orig[a.perm[p]];
+        const double rr = __dsub_rn(bv, amul_row<double>(A, a.x, p));
+        acc[0] = __fma_rn(rr, rr, acc[0]);
+        acc[1] = __fma_rn(bv, bv, acc[1]);
+    }
+    block_reduce_store<2>(acc, a.partials, SL_A, g.bid);
+    if (!group_sync(g)) return false;
+    double t[2];
+    grid_reduce_read<2>(t, a.partials, SL_A, g.nblocks);
+    *out = t[1] > 0.0 ? __ddiv_rn(__dsqrt_rn(t[0]), __dsqrt_rn(t[1])) : __dsqrt_rn(t[0]);
+    return true;
+}
+
 __device__ void phase_store_x(const SolveArgs& a, const Group& g)
 {
     RowIter it = rows_of(g);
@@ -1210,6 +1235,7 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
     spuma_solver_perf pf;
     pf.initial_residual = 0.0;
     pf.final_residual = 0.0;
+    pf.true_rel_residual_l2 = 0.0;
     pf.n_iter = 0;
     pf.n_outer = 0;
     pf.converged = 0;
@@ -1266,12 +1292,19 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
                     pf.singular = sing;
                 }
             }
+            if (ok) {
+                Mat<double> A64 = mat_of<double>(a);
+                if (KIND == KIND_PBICG) A64.ell_w = 0;   // asymmetric: the internal CSR holds A
+                ok = true_residual(a, A64, KIND == KIND_PBICG ? nullptr : a.b, g, &pf.true_rel_residual_l2);
+            }
             if (ok && !a.no_store) phase_store_x(a, g);
         }
     }
     if (g.bid == 0 && threadIdx.x == 0 && a.perf) {
         __threadfence();
         pf.status = ld_volatile_int(a.status);
+        // a group that stopped always has a status; keep the report honest if not
+        if (!ok && pf.status == 0) pf.status = SPUMA_ERR_DEVICE_TIMEOUT;
         if (pf.status != 0) pf.converged = 0;
         *a.perf = pf;
     }
@@ -1280,19 +1313,22 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
 template <int KIND>
 __global__ void __launch_bounds__(1024, 1) k_solve(SolveArgs a, unsigned long long timeout_ns)
 {
-    Group g{reinterpret_cast<unsigned*>(a.status + DS_BARRIER), a.status, (int)gridDim.x, (int)blockIdx.x, timeout_ns};
+    Group g{reinterpret_cast<unsigned long long*>(a.status + DS_BARRIER), a.status, (int)gridDim.x, (int)blockIdx.x, timeout_ns};
     run_system<KIND>(a, g);
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(256, 2) k_solve_batch(BatchTable t, unsigned long long timeout_ns)
+// The batched launch, one instance per solve kind and largest block size
+// (the register budget follows from it: 128 per thread up to 512 threads, 64
+// at 1024).
+template <int KIND, int MAXT>
+__global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1) k_solve_batch(BatchTable t, unsigned long long timeout_ns)
 {
     __shared__ SolveArgs sa;
     int s = 0;
     while (s + 1 < t.n_sys && (int)blockIdx.x >= t.split[s + 1]) s++;
     if (threadIdx.x == 0) sa = *t.args[s];
     __syncthreads();
-    Group g{reinterpret_cast<unsigned*>(sa.status + DS_BARRIER), sa.status, t.split[s + 1] - t.split[s],
+    Group g{reinterpret_cast<unsigned long long*>(sa.status + DS_BARRIER), sa.status, t.split[s + 1] - t.split[s],
             (int)blockIdx.x - t.split[s], timeout_ns};
     run_system<KIND>(sa, g);
 }
@@ -1413,13 +1449,21 @@ static const void* solve_kernel(int kind)
     }
 }
 
-static const void* batch_kernel(int kind)
+template <int MAXT>
+static const void* batch_kernel_t(int kind)
 {
     switch (kind) {
-    case KIND_MIXED: return (const void*)k_solve_batch<KIND_MIXED>;
-    case KIND_MIXED_RESTART: return (const void*)k_solve_batch<KIND_MIXED_RESTART>;
-    default: return (const void*)k_solve_batch<KIND_F64>;
+    case KIND_MIXED: return (const void*)k_solve_batch<KIND_MIXED, MAXT>;
+    case KIND_MIXED_RESTART: return (const void*)k_solve_batch<KIND_MIXED_RESTART, MAXT>;
+    default: return (const void*)k_solve_batch<KIND_F64, MAXT>;
     }
+}
+
+static const void* batch_kernel(int kind, int threads)
+{
+    if (threads <= 256) return batch_kernel_t<256>(kind);
+    if (threads <= 512) return batch_kernel_t<512>(kind);
+    return batch_kernel_t<1024>(kind);
 }
 
 static std::mutex g_occ_mu;
@@ -1428,12 +1472,12 @@ static std::map<int, int> g_occ;   // (kernel, block threads) -> co-resident blo
 int solve_blocks_per_sm(int threads, bool batch, int kind)
 {
     std::lock_guard<std::mutex> lk(g_occ_mu);
-    const int key = (threads * 2 + (batch ? 1 : 0)) * 4 + kind;
+    const int key = (threads * 2 + (batch ? 1 : 0)) * 8 + kind;
     auto it = g_occ.find(key);
     if (it != g_occ.end()) return it->second;
     int nb = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch ? batch_kernel(kind) : solve_kernel(kind),
-                                                                  threads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &nb, batch ? batch_kernel(kind, threads) : solve_kernel(kind), threads, 0);
     if (e != cudaSuccess) nb = 0;
     g_occ[key] = nb;
     return nb;
@@ -1511,7 +1555,7 @@ spuma_status launch_batch_kernel(const BatchTable& t, int grid, int threads, int
     unsigned long long tns = barrier_timeout_ns();
     BatchTable tt = t;
     void* args[] = {(void*)&tt, (void*)&tns};
-    SPUMA_CUDA(cudaLaunchKernelExC(&cfg, batch_kernel(kind), args));
+    SPUMA_CUDA(cudaLaunchKernelExC(&cfg, batch_kernel(kind, threads), args));
     return SPUMA_OK;
 }
 

@@ -81,6 +81,10 @@ def test_batch_matches_oracle_per_system(precision):
     X = [torch.zeros_like(b) for b in B]
     ctl = SolverControls(precond=2, precision=precision, tolerance=1e-10)
     bs = BatchSolve(Ms, D, U, B, X, ctl, autotune=True)
+    assert bs.graph_captured                   # replayed from a CUDA graph, not direct launches
+    # the tuner timed a staged search: every block size that can run, then the split weights, then the grid
+    assert {t["block_threads"] for t in bs.trials} >= {64, 128, 256, 512}
+    assert len(bs.trials) >= 7 and bs.tuned_ms == pytest.approx(min(t["ms"] for t in bs.trials), abs=1e-3)
     bs.run()
     res = bs.results()
     first = [x.clone() for x in X]
@@ -94,11 +98,68 @@ def test_batch_matches_oracle_per_system(precision):
             assert np.linalg.norm(x - xo) <= 1e-10 * np.linalg.norm(xo)
         r = c.b - oracle.amul(m.lower, m.upper_addr, dgs[k], ups[k], x)
         assert np.abs(r).sum() / np.abs(c.b).sum() < 1e-10
+        assert res[k]["true_rel_residual_l2"] == pytest.approx(np.linalg.norm(r) / np.linalg.norm(c.b), rel=1e-12)
     for x in X:
         x.zero_()
     bs.run()                                   # graph replay: same answers bit for bit
     for a, b in zip(first, X):
         assert torch.equal(a, b)
+
+
+def test_batch_without_graph():
+    """The direct-launch replay (no graph) gives the graph's answers bit for bit."""
+    from paper_2512_22215_gb300 import BatchSolve, SolverControls
+    cs = [case(s, jitter=0.2, permute=True, seed=35 + k, lognormal=True) for k, s in enumerate([7, 10, 5])]
+    Ms = [mesh_of(c) for c in cs]
+    ups, dgs = zip(*[assemble_oracle(c) for c in cs])
+    D, U, B = [dev(d) for d in dgs], [dev(u) for u in ups], [dev(c.b) for c in cs]
+    ctl = SolverControls(precond=2, tolerance=1e-10, block_threads=128)
+    X1 = [torch.zeros_like(b) for b in B]
+    g = BatchSolve(Ms, D, U, B, X1, ctl, autotune=False)
+    assert g.graph_captured and g.tuned_ms == -1.0 and g.trials == []
+    g.run()
+    X2 = [torch.zeros_like(b) for b in B]
+    d = BatchSolve(Ms, D, U, B, X2, ctl, autotune=False, graph=False)
+    assert not d.graph_captured
+    d.run()
+    torch.cuda.synchronize()
+    for a, b in zip(X1, X2):
+        assert torch.equal(a, b)
+
+
+@pytest.mark.slow
+def test_batch_64_systems_log_uniform():
+    """The batched workload: 64 jittered, permuted hex blocks with cell counts
+    log-uniform in 1e4..5e5 (sides from hexmesh.batch_sizes, seed 5; 8.2M
+    cells), FP64 and mixed, tuned and replayed from a CUDA graph.  Every system
+    reaches the oracle's FP64 residual 1e-8; FP64 systems of at most 64^3
+    cells match the oracle's PCG at the same iteration count to 1e-10."""
+    from paper_2512_22215_gb300 import MIXED, BatchSolve, LduMesh, SolverControls
+    sides = hexmesh.batch_sizes(64, seed=5)
+    cs = [hexmesh.pressure_case(n, jitter=0.2, permute=True, seed=500 + k, lognormal_gamma=True)
+          for k, n in enumerate(sides)]
+    assert sum(c.mesh.n_cells for c in cs) > 8_000_000
+    Ms = [LduMesh(c.mesh.lower, c.mesh.upper_addr, c.mesh.n_cells, centres=c.mesh.c) for c in cs]
+    ups, dgs = zip(*[assemble_oracle(c) for c in cs])
+    D, U, B = [dev(d) for d in dgs], [dev(u) for u in ups], [dev(c.b) for c in cs]
+    for precision in (0, MIXED):
+        X = [torch.zeros_like(b) for b in B]
+        bs = BatchSolve(Ms, D, U, B, X, SolverControls(precond=2, precision=precision, tolerance=1e-8))
+        assert bs.graph_captured
+        bs.run()
+        res = bs.results()
+        for k, c in enumerate(cs):
+            m = c.mesh
+            assert res[k]["status"] == 0 and res[k]["converged"] == 1, (k, res[k])
+            x = X[k].cpu().numpy()
+            r = c.b - oracle.amul(m.lower, m.upper_addr, dgs[k], ups[k], x)
+            assert np.abs(r).sum() / np.abs(c.b).sum() < 1e-8
+            assert res[k]["true_rel_residual_l2"] == pytest.approx(np.linalg.norm(r) / np.linalg.norm(c.b),
+                                                                   rel=1e-12)
+            if precision == 0 and m.n_cells <= 64 ** 3:
+                xo, _ = oracle.pcg(m.lower, m.upper_addr, dgs[k], ups[k], c.b, precond=2, tol=0.0,
+                                   max_iter=res[k]["n_iter"])
+                assert np.linalg.norm(x - xo) <= 1e-10 * np.linalg.norm(xo), k
 
 
 def test_autograd_dense_gradient_8cubed():
@@ -126,7 +187,7 @@ def test_autograd_dense_gradient_8cubed():
     assert np.allclose(dg.grad.cpu().numpy(), np.diag(G), rtol=1e-8, atol=1e-11 * np.abs(G).max())
 
 
-@pytest.mark.parametrize("n", [64])
+@pytest.mark.parametrize("n", [64, pytest.param(128, marks=pytest.mark.slow)])
 def test_autograd_finite_differences(n):
     """32 random directions, central differences with step 1e-6 (relative to the
     perturbed quantity), FP64 solves to 1e-14; agreement to 1e-6 relative."""

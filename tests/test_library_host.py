@@ -30,7 +30,7 @@ def header_functions():
 def test_header_is_plain_c(tmp_path):
     src = tmp_path / "t.c"
     src.write_text('#include "spuma.h"\nint main(void){ spuma_solver_controls c; spuma_solver_perf p;'
-                   ' (void)c; (void)p; return (int)sizeof(spuma_solver_perf) - 40; }\n')
+                   ' (void)c; (void)p; return (int)sizeof(spuma_solver_perf) - 48; }\n')
     exe = tmp_path / "t"
     subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
     assert subprocess.run([str(exe)]).returncode == 0
@@ -102,15 +102,48 @@ def test_batch_split(L):
 
 def test_tune_cache_roundtrip(L, tmp_path):
     path = str(tmp_path / "tune.json").encode()
-    t, p, ms = C.c_int32(), C.c_int32(), C.c_double()
-    assert L.spuma_tune_cache_lookup(path, b"sig-a", C.byref(t), C.byref(p), C.byref(ms)) == 0
-    assert L.spuma_tune_cache_store(path, b"sig-a", 256, 1, 12.5) == 1
-    assert L.spuma_tune_cache_store(path, b"sig-b", 512, 0, 3.25) == 1
+    t, p, d, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
+    assert L.spuma_tune_cache_lookup(path, b"sig-a", C.byref(t), C.byref(p), C.byref(d), C.byref(ms)) == 0
+    assert L.spuma_tune_cache_store(path, b"sig-a", 256, 1, 1, 12.5) == 1
+    assert L.spuma_tune_cache_store(path, b"sig-b", 512, 0, 2, 3.25) == 1
+    assert L.spuma_tune_cache_store(path, b"sig-c", 512, 0, 0, 3.25) == 0      # grid divisor >= 1
     import json
     data = json.loads(open(path).read())
-    assert data == {"sig-a": [256, 1, 12.5], "sig-b": [512, 0, 3.25]}
-    assert L.spuma_tune_cache_lookup(path, b"sig-b", C.byref(t), C.byref(p), C.byref(ms)) == 1
-    assert (t.value, p.value, ms.value) == (512, 0, 3.25)
+    assert data == {"sig-a": [256, 1, 1, 12.5], "sig-b": [512, 0, 2, 3.25]}
+    assert L.spuma_tune_cache_lookup(path, b"sig-b", C.byref(t), C.byref(p), C.byref(d), C.byref(ms)) == 1
+    assert (t.value, p.value, d.value, ms.value) == (512, 0, 2, 3.25)
+
+
+def test_tune_cache_reads_three_number_lines(L, tmp_path):
+    """Entries of the older [threads, policy, ms] form read with grid divisor 1."""
+    path = tmp_path / "old.json"
+    path.write_text('{\n  "sig-old": [128, 0, 7.500000]\n}\n')
+    t, p, d, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
+    assert L.spuma_tune_cache_lookup(str(path).encode(), b"sig-old", C.byref(t), C.byref(p), C.byref(d),
+                                     C.byref(ms)) == 1
+    assert (t.value, p.value, d.value, ms.value) == (128, 0, 1, 7.5)
+
+
+def test_batch_create_rejects_unknown_flags(L):
+    from paper_2512_22215_gb300._lib import Controls
+    ctl = Controls(2, 0, 1e-8, 0.0, 1e-4, 100, 0, 10, 0)
+    one = (C.c_void_p * 1)(1)
+    h = C.c_void_p()
+    assert L.spuma_batch_create(1, one, one, one, one, one, C.byref(ctl), 1, 8, None, C.byref(h)) == 1
+    assert L.spuma_batch_info(None, None, None, None, None) == 1
+    assert L.spuma_batch_trials(None, 0, None, None, None, None) == 0
+
+
+def test_static_solve_checks_arguments_before_the_device(L):
+    """The no-allocation solve rejects bad controls and NULL arrays on the
+    host, before it looks at its shared static array (no device call)."""
+    from paper_2512_22215_gb300._lib import Controls
+    bad = Controls(9, 0, 1e-8, 0.0, 1e-4, 100, 0, 10, 0)
+    assert L.spuma_pcg_solve_static(8, 12, None, None, None, None, None, None, None, None, None) == 1
+    assert L.spuma_pcg_solve_static(8, 12, 1, 1, 1, 1, 1, 1, C.byref(bad), None, None) == 1
+    ok = Controls(2, 0, 1e-8, 0.0, 1e-4, 100, 0, 10, 0)
+    assert L.spuma_pcg_solve_static(8, 12, None, 1, 1, 1, 1, 1, C.byref(ok), None, None) == 1
+    assert L.spuma_pcg_solve_static(-1, 0, None, None, None, None, None, None, C.byref(ok), None, None) == 1
 
 
 def test_launch_counter_and_timeout_setter(L):

@@ -1,8 +1,10 @@
 """The solve entry point that allocates no device memory, for callers that
 cannot call cudaMalloc (its workspace is a static device array inside the
 library).  Called through the C ABI and checked against the regular entry
-point (spuma_ldu_create + spuma_pcg_solve) on two calls in a row.  This file
-is collected last on purpose."""
+point (spuma_ldu_create + spuma_pcg_solve) on two calls in a row, and against
+the oracle's FP64 DIC-PCG at the same iteration count (relative solution
+error within 1e-10, the FP64 bound of the other parity tests).  This file is
+collected last on purpose."""
 import ctypes as C
 
 import numpy as np
@@ -44,6 +46,9 @@ def test_static_solve_matches_regular_solve_twice():
         assert p["status"] == 0 and p["converged"] == 1
         assert p["n_iter"] == p_ref["n_iter"]
         assert torch.linalg.norm(x - x_ref) <= 1e-10 * torch.linalg.norm(x_ref)
+        xo, _ = oracle.pcg(m.lower, m.upper_addr, dg, up, c.b, precond=2, tol=0.0, max_iter=p["n_iter"])
+        xs = x.cpu().numpy()
+        assert np.linalg.norm(xs - xo) <= 1e-10 * np.linalg.norm(xo)
 
 
 def test_static_solve_rejects_oversized_mesh():
@@ -56,3 +61,6 @@ def test_static_solve_rejects_oversized_mesh():
     st = L.spuma_pcg_solve_static(n, 3 * n, None, None, None, None, None, None, C.byref(cctl), None, None)
     assert st == 4
     assert b"static workspace" in L.spuma_last_error()
+    # a mesh that fits, with no controls: rejected before the array is touched
+    st = L.spuma_pcg_solve_static(8, 12, None, None, None, None, None, None, None, None, None)
+    assert st == 1
