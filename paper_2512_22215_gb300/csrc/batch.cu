@@ -19,7 +19,7 @@ namespace spuma {
 SolveArgs make_args(spuma_ldu_t h);
 void fill_controls(SolveArgs& a, const spuma_solver_controls* ctl);
 bool ctl_ok(const spuma_solver_controls* c);
-int solve_blocks_per_sm(int threads, bool batch, int kind);
+int solve_blocks_per_sm(int threads, bool batch, int kind, size_t dyn = 0);
 int batch_kind(int precision);
 spuma_status launch_batch_kernel(const BatchTable& t, int grid, int threads, int kind, cudaStream_t s);
 
