@@ -62,6 +62,8 @@ def _declare(L):
     L.oracle_dot.restype = _f64
     L.oracle_jacobi_sweep.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
     L.oracle_jacobi_sweep.restype = None
+    L.oracle_gs2_sweep.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+    L.oracle_gs2_sweep.restype = None
     L.oracle_amul_asym.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p, _f64p]
     L.oracle_amul_asym.restype = None
     L.oracle_dilu_factor.argtypes = [_i32, _i32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
@@ -241,6 +243,16 @@ def jacobi_sweep(l, u, diag, upper, wrd, r, e):
     q = np.empty(len(diag))
     lib().oracle_jacobi_sweep(len(diag), len(l), _c(l, np.int32), _c(u, np.int32), _c(diag, np.float64),
                               _c(upper, np.float64), _c(wrd, np.float64), _c(r, np.float64), e, q)
+    return e
+
+
+def gs2_sweep(l, u, diag, upper, rD, r, e):
+    """One two-stage Gauss-Seidel sweep in place: e += (D^-1 - D^-1 L D^-1)(r - A e),
+    in the face order of oracle.c (rD = 1/d)."""
+    n = len(diag)
+    q, y = np.empty(n), np.empty(n)
+    lib().oracle_gs2_sweep(n, len(l), _c(l, np.int32), _c(u, np.int32), _c(diag, np.float64),
+                           _c(upper, np.float64), _c(rD, np.float64), _c(r, np.float64), e, q, y)
     return e
 
 

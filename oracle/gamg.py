@@ -1,7 +1,9 @@
 """GAMG oracle (test infrastructure only): the paper's production pressure
 solver, "GAMG, smoother Richardson" (fvSolution listing; Sec. 4.3 and the
 smoother table: Richardson = damped Jacobi on every level, diagonal-PCG at
-the coarsest one; the coarsening is OpenFOAM's, unmodified).
+the coarsest one; the coarsening is OpenFOAM's, unmodified), and the table's
+other two options: the two-stage Gauss-Seidel smoother and DIC-PCG at the
+coarsest level (the profiling run's "coarsestSolver=DIC+PCG").
 
 Plain, slow, sequential Python over numpy arrays, FP64, each sum in the order
 written here.  Only the tests may call it.
@@ -27,8 +29,15 @@ Reading (the paper names the method, not its parameters):
                  aggregate, ascending), e = prolongation of V(k+1, r_c)
                  (injection) scaled by its A-norm optimal step
                  (e.r)/(e.Ae) (OpenFOAM's correction scaling; kept unscaled
-                 when e.Ae <= 0), then NU_POST damped-Jacobi sweeps
-                 e_i += (OMEGA rD_i) (r_i - (A e)_i)  (one FMA, rD = 1/d).
+                 when e.Ae <= 0), then NU_POST smoothing sweeps:
+                 Richardson: damped Jacobi e_i += (OMEGA rD_i) (r_i - (A e)_i)
+                 (one FMA, rD = 1/d);
+                 two-stage Gauss-Seidel (smoother="gs2", Berger-Vergiat et
+                 al.): e += (D^-1 - D^-1 L D^-1)(r - A e), i.e. the
+                 Gauss-Seidel lower solve approximated by one Jacobi step and
+                 one Jacobi-Richardson sweep, undamped (oracle.c gs2_sweep).
+  coarsest       PCG from 0 to COARSE_REL_TOL with the diagonal (default) or
+                 the DIC preconditioner (coarsest_precond=2).
   solver         x0 given; r = b - A x; normFactor, residual and the
                  stopping rule of PCG; each iteration x += V(0, r), r = b - A x.
 """
@@ -36,7 +45,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import amul, dot, jacobi_sweep, norm_factor, pcg
+from . import amul, dot, gs2_sweep, jacobi_sweep, norm_factor, pcg
 
 OMEGA = 2.0 / 3.0
 NU_POST = 2
@@ -148,32 +157,40 @@ def matrices(levels, diag, upper):
     return mats
 
 
-def vcycle(levels, mats, k, r):
+def vcycle(levels, mats, k, r, smoother="richardson", coarsest_precond=1):
     lv = levels[k]
     d, up = mats[k]
     if k == len(levels) - 1:
-        e, _ = pcg(lv["l"], lv["u"], d, up, r, precond=1, tol=0.0, rel_tol=COARSE_REL_TOL,
+        e, _ = pcg(lv["l"], lv["u"], d, up, r, precond=coarsest_precond, tol=0.0, rel_tol=COARSE_REL_TOL,
                    max_iter=2 * lv["n"] + 10)
         return e
     nc = levels[k + 1]["n"]
     rc = np.zeros(nc)
     for i in range(lv["n"]):
         rc[lv["agg"][i]] += r[i]
-    ec = vcycle(levels, mats, k + 1, rc)
+    ec = vcycle(levels, mats, k + 1, rc, smoother, coarsest_precond)
     e = np.ascontiguousarray(ec[lv["agg"]], dtype=np.float64)
     # scale the prolongated correction by its A-norm optimal step (e.r)/(e.Ae)
     q = amul(lv["l"], lv["u"], d, up, e)
     eq = dot(e, q)
     if eq > 0.0:
         e = e * (dot(e, r) / eq)
-    wrd = OMEGA * (1.0 / d)
-    for _ in range(NU_POST):
-        jacobi_sweep(lv["l"], lv["u"], d, up, wrd, r, e)
+    if smoother == "gs2":
+        rD = 1.0 / d
+        for _ in range(NU_POST):
+            gs2_sweep(lv["l"], lv["u"], d, up, rD, r, e)
+    else:
+        wrd = OMEGA * (1.0 / d)
+        for _ in range(NU_POST):
+            jacobi_sweep(lv["l"], lv["u"], d, up, wrd, r, e)
     return e
 
 
-def gamg(l, u, diag, upper, b, weight, x0=None, tol=1e-8, rel_tol=0.0, max_iter=300, min_iter=0):
-    """(x, perf, levels) of the GAMG solver with the PCG residual and stopping rule."""
+def gamg(l, u, diag, upper, b, weight, x0=None, tol=1e-8, rel_tol=0.0, max_iter=300, min_iter=0,
+         smoother="richardson", coarsest_precond=1):
+    """(x, perf, levels) of the GAMG solver with the PCG residual and stopping rule;
+    smoother "richardson" or "gs2", coarsest-level PCG preconditioner 1 (diagonal) or 2 (DIC)."""
+    assert smoother in ("richardson", "gs2") and coarsest_precond in (1, 2)
     n = len(diag)
     levels = hierarchy(n, l, u, weight)
     mats = matrices(levels, diag, upper)
@@ -190,7 +207,7 @@ def gamg(l, u, diag, upper, b, weight, x0=None, tol=1e-8, rel_tol=0.0, max_iter=
 
     if min_iter > 0 or not conv(res0):
         while True:
-            x = x + vcycle(levels, mats, 0, r)
+            x = x + vcycle(levels, mats, 0, r, smoother, coarsest_precond)
             r = b - amul(l, u, diag, upper, x)
             res = np.abs(r).sum() / nfac
             it += 1

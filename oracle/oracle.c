@@ -825,5 +825,25 @@ void oracle_jacobi_sweep(int32_t n, int32_t nf, const int32_t* l, const int32_t*
     for (int32_t i = 0; i < n; i++) e[i] = fma(wrd[i], r[i] - q[i], e[i]);
 }
 
+/* One two-stage Gauss-Seidel sweep of the GAMG smoother (the paper's second
+ * parallel smoother, Sec. 4.3, after Berger-Vergiat et al.): the Gauss-Seidel
+ * step e += (D + L)^-1 (r - A e) with the lower-triangular solve replaced by
+ * one Jacobi step and one Jacobi-Richardson sweep:
+ *   q = r - A e (oracle_amul, then one subtraction per row);
+ *   y_i = rD_i q_i  (rD = 1/d);
+ *   s_u = q_u - sum_{f: u(f) = u} upper_f y_{l(f)}, f ascending, one FMA per term;
+ *   e_i = e_i + rD_i s_i.
+ * (D + L)^-1 ~ D^-1 - D^-1 L D^-1; L is A's strictly lower part (row u(f),
+ * column l(f), coefficient upper_f).  q and y are scratch.                 */
+void oracle_gs2_sweep(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, const double* diag,
+                      const double* upper, const double* rD, const double* r, double* e, double* q, double* y)
+{
+    oracle_amul(n, nf, l, u, diag, upper, e, q);
+    for (int32_t i = 0; i < n; i++) q[i] = r[i] - q[i];
+    for (int32_t i = 0; i < n; i++) y[i] = rD[i] * q[i];
+    for (int32_t f = 0; f < nf; f++) q[u[f]] = fma(-upper[f], y[l[f]], q[u[f]]);
+    for (int32_t i = 0; i < n; i++) e[i] = e[i] + rD[i] * q[i];
+}
+
 /* sum_i a_i b_i in ascending order (GAMG correction scaling). */
 double oracle_dot(int32_t n, const double* a, const double* b) { return sum_prod(n, a, b); }

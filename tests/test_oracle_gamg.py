@@ -116,3 +116,86 @@ def test_iterations_do_not_grow_with_the_mesh():
         _, p, _ = G.gamg(m.lower, m.upper_addr, dg, up, c.b, w, tol=1e-10)
         its.append(p["n_iter"])
     assert its[1] <= 1.3 * its[0]
+
+
+def _dense(n, l, u, d, a):
+    A = np.zeros((n, n))
+    A[np.arange(n), np.arange(n)] = d
+    A[l, u] = a
+    A[u, l] = a
+    return A
+
+
+def test_gs2_sweep_is_the_truncated_gauss_seidel_step_dense():
+    """The face-loop sweep equals the matrix formula e + (D^-1 - D^-1 L D^-1)(r - A e)
+    with L = strictly lower part of A (row u(f), column l(f)), on a jittered
+    permuted mesh (dense numpy, independent of the face loop)."""
+    c, m, up, dg, w = _case((5, 4, 3), 96, jitter=0.2, permute=True, lognormal_gamma=True)
+    n = m.n_cells
+    A = _dense(n, m.lower, m.upper_addr, dg, up)
+    L = np.tril(A, -1)
+    Dinv = np.diag(1.0 / dg)
+    rng = np.random.default_rng(97)
+    r, e0 = rng.standard_normal(n), rng.standard_normal(n)
+    e = oracle.gs2_sweep(m.lower, m.upper_addr, dg, up, 1.0 / dg, r, e0.copy())
+    ref = e0 + (Dinv - Dinv @ L @ Dinv) @ (r - A @ e0)
+    assert np.allclose(e, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    # a sign error in L, or the upper part used instead, is far off
+    bad = e0 + (Dinv + Dinv @ L @ Dinv) @ (r - A @ e0)
+    assert not np.allclose(e, bad, rtol=1e-6)
+
+
+def test_gs2_special_cases():
+    # no faces: one sweep is the Jacobi solve rD r from e = 0 (both stages give rD r, rounded once)
+    d = np.array([2.0, 4.0, 5.0])
+    r = np.array([1.0, 2.0, 3.0])
+    e = oracle.gs2_sweep(np.zeros(0, np.int64), np.zeros(0, np.int64), d, np.zeros(0), 1.0 / d, r, np.zeros(3))
+    assert np.array_equal(e, (1.0 / d) * r) and np.allclose(e, [0.5, 0.5, 0.6], rtol=1e-15)
+    # two cells joined by one face: the truncated series is exact for a 2x2 lower solve,
+    # so from e = 0 the sweep is the Gauss-Seidel step (D + L)^-1 r
+    d = np.array([4.0, 3.0])
+    a = np.array([-1.0])
+    r = np.array([1.0, 2.0])
+    e = oracle.gs2_sweep(np.array([0]), np.array([1]), d, a, 1.0 / d, r, np.zeros(2))
+    DL = np.array([[4.0, 0.0], [-1.0, 3.0]])
+    assert np.allclose(e, np.linalg.solve(DL, r), rtol=1e-15)
+
+
+@pytest.mark.parametrize("smoother,coarsest", [("gs2", 1), ("richardson", 2), ("gs2", 2)])
+def test_gamg_options_match_dense_solution(smoother, coarsest):
+    c, m, up, dg, w = _case(6, 98, jitter=0.2, permute=True, lognormal_gamma=True)
+    x, p, levels = G.gamg(m.lower, m.upper_addr, dg, up, c.b, w, tol=1e-13, max_iter=500, smoother=smoother,
+                          coarsest_precond=coarsest)
+    A = _dense(m.n_cells, m.lower, m.upper_addr, dg, up)
+    assert p["converged"] == 1 and len(levels) >= 3
+    assert np.allclose(x, np.linalg.solve(A, c.b), rtol=1e-9, atol=1e-11)
+
+
+def test_gamg_single_level_is_the_coarsest_pcg():
+    """A mesh of at most N_COARSEST cells has one level: one GAMG iteration is one
+    coarsest-level PCG solve from 0 (DIC or diagonal) to COARSE_REL_TOL."""
+    c, m, up, dg, w = _case((3, 3, 1), 99, jitter=0.2, permute=True, lognormal_gamma=True)
+    assert m.n_cells <= G.N_COARSEST
+    for pc in (1, 2):
+        x, p, levels = G.gamg(m.lower, m.upper_addr, dg, up, c.b, w, tol=0.0, max_iter=1, coarsest_precond=pc)
+        assert len(levels) == 1
+        xo, _ = oracle.pcg(m.lower, m.upper_addr, dg, up, c.b, precond=pc, tol=0.0, rel_tol=G.COARSE_REL_TOL,
+                           max_iter=2 * m.n_cells + 10)
+        assert np.array_equal(x, xo)
+
+
+def test_gs2_gamg_error_decreases_in_energy_norm_and_iterations_do_not_grow():
+    c, m, up, dg, w = _case(6, 93, jitter=0.2, permute=True, lognormal_gamma=True)
+    xs, _ = oracle.pcg(m.lower, m.upper_addr, dg, up, c.b, tol=1e-15, max_iter=5000)
+    errs = []
+    for it in range(1, 6):
+        x, _, _ = G.gamg(m.lower, m.upper_addr, dg, up, c.b, w, tol=0.0, max_iter=it, smoother="gs2")
+        e = x - xs
+        errs.append(np.dot(e, oracle.amul(m.lower, m.upper_addr, dg, up, e)))
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    its = []
+    for n in (8, 16):
+        c, m, up, dg, w = _case(n, 95, jitter=0.2, permute=True, lognormal_gamma=True)
+        _, p, _ = G.gamg(m.lower, m.upper_addr, dg, up, c.b, w, tol=1e-10, smoother="gs2", coarsest_precond=2)
+        its.append(p["n_iter"])
+    assert its[1] <= 1.3 * its[0], its
