@@ -8,8 +8,10 @@
  * Every loop runs in the order the method states it: faces ascending (or
  * descending for the backward DIC sweep), cells ascending.  Build with
  * -O2 -ffp-contract=off so that the compiler fuses nothing; where the method
- * is read as a fused multiply-add (the row sums of Amul and the DIC sweeps)
- * the code calls fma()/fmaf() explicitly.
+ * is read as a fused multiply-add (the row sums of Amul and the DIC sweeps,
+ * and the Krylov vector recurrences x += alpha p, r -= alpha q, p = w + beta p
+ * of PCG, PBiCG and the mixed forms, as an FMA-contracting build of
+ * OpenFOAM computes them) the code calls fma()/fmaf() explicitly.
  *
  * Matrix: OpenFOAM's lduMatrix ("LDUorderedCOO", paper Sec. 2.1): diag[N],
  * upper[F] (symmetric, lower == upper), lowerAddr l[F] (owner) and upperAddr
@@ -278,15 +280,15 @@ int32_t oracle_pcg(int32_t n, int32_t nf, const int32_t* l, const int32_t* u,
                 for (int32_t i = 0; i < n; i++) p[i] = w[i];
             } else {
                 double beta = rho / rho_old;
-                for (int32_t i = 0; i < n; i++) p[i] = w[i] + beta * p[i];
+                for (int32_t i = 0; i < n; i++) p[i] = fma(beta, p[i], w[i]);
             }
             oracle_amul(n, nf, l, u, diag, upper, p, q);
             double sigma = sum_prod(n, q, p);
             if (fabs(sigma) / nfac < 1e-300) { singular = 1; break; }
             double alpha = rho / sigma;
             for (int32_t i = 0; i < n; i++) {
-                x[i] += alpha * p[i];
-                r[i] -= alpha * q[i];
+                x[i] = fma(alpha, p[i], x[i]);
+                r[i] = fma(-alpha, q[i], r[i]);
             }
             res = sum_mag(n, r) / nfac;
         } while ((++it < max_iter && !converged(res, res0, tol, rel_tol)) || it < min_iter);
@@ -388,21 +390,21 @@ int32_t oracle_mixed_ir(int32_t n, int32_t nf, const int32_t* l, const int32_t* 
                 for (int32_t i = 0; i < n; i++) p[i] = w[i];
             } else {
                 float beta = (float)(rho / rho_old);
-                for (int32_t i = 0; i < n; i++) p[i] = w[i] + beta * p[i];
+                for (int32_t i = 0; i < n; i++) p[i] = fmaf(beta, p[i], w[i]);
             }
             oracle_amul_f32(n, nf, l, u, d32, u32, p, q);
             double sigma = sum_prod_f32(n, q, p);
             if (fabs(sigma) / infac < 1e-300) { singular = 1; break; }
             float alpha = (float)(rho / sigma);
             for (int32_t i = 0; i < n; i++) {
-                di[i] += alpha * p[i];
-                ri[i] -= alpha * q[i];
+                di[i] = fmaf(alpha, p[i], di[i]);
+                ri[i] = fmaf(-alpha, q[i], ri[i]);
             }
             ires = sum_mag_f32(n, ri) / infac;
             it++;
         } while (it < max_iter && !(ires < inner_rel_tol * ires0));
         total_it += it;
-        for (int32_t i = 0; i < n; i++) x[i] += s * (double)di[i];
+        for (int32_t i = 0; i < n; i++) x[i] = fma(s, (double)di[i], x[i]);
         outer++;
     }
 done:
@@ -501,15 +503,15 @@ int32_t oracle_mixed_reliable(int32_t n, int32_t nf, const int32_t* l, const int
             for (int32_t i = 0; i < n; i++) p[i] = w[i];
         } else {
             float beta = (float)(rho / rho_old);
-            for (int32_t i = 0; i < n; i++) p[i] = w[i] + beta * p[i];
+            for (int32_t i = 0; i < n; i++) p[i] = fmaf(beta, p[i], w[i]);
         }
         oracle_amul_f32(n, nf, l, u, d32, u32, p, q);
         double sigma = sum_prod_f32(n, q, p);
         if (fabs(sigma) / nfac < 1e-300) { singular = 1; break; }
         float alpha = (float)(rho / sigma);
         for (int32_t i = 0; i < n; i++) {
-            xs[i] += alpha * p[i];
-            r[i] -= alpha * q[i];
+            xs[i] = fmaf(alpha, p[i], xs[i]);
+            r[i] = fmaf(-alpha, q[i], r[i]);
         }
         it++;
         double ress = sum_mag_f32(n, r) / nfac;
@@ -788,8 +790,8 @@ int32_t oracle_pbicg(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, 
             } else {
                 double beta = wArA / wArA_old;
                 for (int32_t i = 0; i < n; i++) {
-                    pA[i] = wA[i] + beta * pA[i];
-                    pT[i] = wT[i] + beta * pT[i];
+                    pA[i] = fma(beta, pA[i], wA[i]);
+                    pT[i] = fma(beta, pT[i], wT[i]);
                 }
             }
             oracle_amul_asym(n, nf, l, u, diag, lower, upper, pA, wA);
@@ -798,9 +800,9 @@ int32_t oracle_pbicg(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, 
             if (fabs(wApT) / nfac < 1e-300) { singular = 1; break; }
             double alpha = wArA / wApT;
             for (int32_t i = 0; i < n; i++) {
-                x[i] += alpha * pA[i];
-                rA[i] -= alpha * wA[i];
-                rT[i] -= alpha * wT[i];
+                x[i] = fma(alpha, pA[i], x[i]);
+                rA[i] = fma(-alpha, wA[i], rA[i]);
+                rT[i] = fma(-alpha, wT[i], rT[i]);
             }
             res = sum_mag(n, rA) / nfac;
         } while ((++it < max_iter && !converged(res, res0, tol, rel_tol)) || it < min_iter);
