@@ -385,6 +385,19 @@ spuma_status spuma_pbicg_solve(spuma_ldu_t h, const double* diag, const double* 
  *   The hierarchy's handle h must outlive the GAMG object; its status and
  *   barrier words are shared with h's other calls (stream-ordered).
  * ---------------------------------------------------------------------- */
+/* spuma_gamg_set_options: the smoother of later solves, SPUMA_GAMG_RICHARDSON
+ *   (default; damped Jacobi as above) or SPUMA_GAMG_GAUSS_SEIDEL_2STAGE (the
+ *   paper's second parallel smoother, after Berger-Vergiat et al.: each sweep
+ *   q = r - A e, y = q/d, e_i += (q_i - sum over the row's lower entries in
+ *   face order of a_f y_col)/d_i, the Gauss-Seidel lower solve replaced by one
+ *   Jacobi step and one Jacobi-Richardson sweep; 1/d rounded once, each
+ *   product rounded, one FMA per lower term), and the coarsest level's PCG
+ *   preconditioner, SPUMA_PRECOND_DIAGONAL (default) or SPUMA_PRECOND_DIC
+ *   (the profiling run's "coarsestSolver=DIC+PCG"; factor and sweeps in the
+ *   sequential face order, by one thread: the coarsest level has about ten
+ *   cells).  Host only; no device work. */
+#define SPUMA_GAMG_RICHARDSON 0
+#define SPUMA_GAMG_GAUSS_SEIDEL_2STAGE 1
 typedef struct spuma_gamg* spuma_gamg_t;
 spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_stream_t stream, spuma_gamg_t* out);
 size_t spuma_gamg_workspace_bytes(spuma_gamg_t g);
@@ -392,6 +405,7 @@ spuma_status spuma_gamg_bind(spuma_gamg_t g, void* workspace, size_t workspace_b
 spuma_status spuma_gamg_info(spuma_gamg_t g, int32_t* n_levels, int32_t* level_cells, int32_t max_levels);
 spuma_status spuma_gamg_solve(spuma_gamg_t g, const double* diag, const double* upper, const double* b, double* x,
                               const spuma_solver_controls* ctl, spuma_solver_perf* perf, spuma_stream_t stream);
+spuma_status spuma_gamg_set_options(spuma_gamg_t g, int32_t smoother, int32_t coarsest_precond);
 spuma_status spuma_gamg_destroy(spuma_gamg_t g);
 
 /* ------------------------------------------------------------------------

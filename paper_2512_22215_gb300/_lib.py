@@ -20,6 +20,7 @@ F64, MIXED, F32, MIXED_RESTART = 0, 1, 2, 3
 PRECOND_NONE, PRECOND_DIAGONAL, PRECOND_DIC, PRECOND_DILU = 0, 1, 2, 3
 WORKSPACE_ASYMMETRIC = 1
 BATCH_AUTOTUNE, BATCH_ALLOW_DIRECT, BATCH_NO_GRAPH = 1, 2, 4
+GAMG_RICHARDSON, GAMG_GAUSS_SEIDEL_2STAGE = 0, 1
 
 
 class Controls(C.Structure):
@@ -77,6 +78,7 @@ _SIGS = {
     "spuma_gamg_bind": (_I, [_H, _P, C.c_size_t, _P]),
     "spuma_gamg_info": (_I, [_H, C.POINTER(_I), _P, _I]),
     "spuma_gamg_solve": (_I, [_H, _P, _P, _P, _P, C.POINTER(Controls), _P, _P]),
+    "spuma_gamg_set_options": (_I, [_H, _I, _I]),
     "spuma_gamg_destroy": (_I, [_H]),
     "spuma_pbicg_solve": (_I, [_H, _P, _P, _P, _P, _P, C.POINTER(Controls), _P, _P]),
     "spuma_pcg_adjoint": (_I, [_H, _P, _P, _P, _P, _P, _P, _P, C.POINTER(Controls), _P, _P]),

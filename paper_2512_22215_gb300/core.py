@@ -255,7 +255,9 @@ class GamgSolver:
     """GAMG for a mesh's symmetric pressure matrices: the level hierarchy from
     the face weights (e.g. |S_f|), built once, then any number of solves."""
 
-    def __init__(self, mesh: LduMesh, face_weight):
+    def __init__(self, mesh: LduMesh, face_weight, smoother: int = 0, coarsest_precond: int = 1):
+        """smoother 0 Richardson (damped Jacobi), 1 two-stage Gauss-Seidel;
+        coarsest_precond 1 diagonal, 2 DIC."""
         L = lib()
         self.mesh = mesh
         fw = torch.as_tensor(face_weight, dtype=torch.float64).to(mesh.device).contiguous()
@@ -266,6 +268,7 @@ class GamgSolver:
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=mesh.device)
         base = (self.workspace.data_ptr() + 255) // 256 * 256
         check(L.spuma_gamg_bind(h, base, nbytes, stream_ptr()), "spuma_gamg_bind")
+        check(L.spuma_gamg_set_options(h, int(smoother), int(coarsest_precond)), "spuma_gamg_set_options")
         nl = C.c_int32()
         cells = (C.c_int32 * 64)()
         check(L.spuma_gamg_info(h, C.byref(nl), C.cast(cells, C.c_void_p), 64), "spuma_gamg_info")

@@ -79,54 +79,6 @@ __device__ __forceinline__ int ld_volatile_int(const int* p)
     return *(const volatile int*)p;
 }
 
-// ------------------------------------------------ bulk copies (sm_90+) --
-// One-dimensional bulk copies global -> shared, completed on an mbarrier
-// (transaction bytes), as the DIC sweeps' staging ring uses them.  Source,
-// destination and size must be multiples of 16 bytes.
-__device__ __forceinline__ unsigned smem_u32(const void* p)
-{
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-// Makes the mbarrier initialisation visible to the bulk-copy (async) proxy.
-__device__ __forceinline__ void fence_mbar_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes)
-{
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
-                     smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-// Orders this thread's earlier generic-proxy global writes before later
-// bulk-copy (async-proxy) reads of them, once a barrier has passed.
-__device__ __forceinline__ void fence_proxy_async_global()
-{
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
 // Fused multiply-add in the working precision.
 __device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
@@ -327,6 +279,8 @@ struct Layout {
     size_t x32, r32, w32, p32, q32;
     // control
     size_t partials, bar, status, args, clk;
+    // cached per-cell boundary-face lists (pressure-step operators)
+    size_t bstart, blist, blist_cap;
     // asymmetric matrices (PBiCG), present when the workspace was sized with
     // SPUMA_WORKSPACE_ASYMMETRIC: A^T's coefficients in the internal CSR, the
     // transposed DILU sweep coefficients, the transposed search direction
@@ -347,6 +301,8 @@ struct spuma_ldu {
     size_t ws_bytes = 0;
     spuma::Layout L;
     int prepared_precond = -1;
+    const int32_t* bl_cell = nullptr;  // boundary (bface_cell pointer, count) whose lists are cached
+    int32_t bl_nb = -1;
     int ell_w = 0;                     // width of the fixed-width Amul layout (0: not used)
     std::vector<int32_t> h_lvl;
     template <class T>

@@ -74,83 +74,99 @@ __global__ void k_fv_bsort(int n, const int* __restrict__ bstart, int* blist)
     }
 }
 
-// Gauss linear gradient: grad_i = (1/V_i) sum_f S_f p_f with the outward S
-// (+S_f for the owner, -S_f for the neighbour); boundary p_b = 0 on
-// Dirichlet faces, p_cell on zero-gradient ones.
-__global__ void k_fv_grad(int n, const int* __restrict__ lo_start, const int* __restrict__ lo_face,
-                          const int* __restrict__ own_start, const int* __restrict__ l, const int* __restrict__ u,
-                          const double* __restrict__ sf, const double* __restrict__ w, const double* __restrict__ p,
-                          const int* __restrict__ bstart, const int* __restrict__ blist,
-                          const double* __restrict__ bsf, const int8_t* __restrict__ btype,
-                          const double* __restrict__ v, double* __restrict__ grad)
+// Gauss linear gradient, in two passes.  Face pass (face order, coalesced):
+// t_f = S_f p_f with p_f = w p_l + (1 - w) p_u, each component a rounded
+// product, padded to 32 bytes (one sector per face).  Cell pass: grad_i =
+// (1/V_i) (sum over the neighbour-side faces of -t_f, then the owner-side
+// faces of +t_f, ascending face order, then S_b p_b over the boundary faces,
+// p_b = 0 on Dirichlet faces, p_i on zero-gradient ones).  The sequential
+// loop computes the same p_f and S_f p_f from either side of a face, so the
+// result is bit-identical to it.
+__global__ void __launch_bounds__(256, 8) k_fv_grad_face(int nf, const int* __restrict__ l,
+                                                         const int* __restrict__ u, const double* __restrict__ sf,
+                                                         const double* __restrict__ w, const double* __restrict__ p,
+                                                         double4* __restrict__ t)
+{
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
+        const double wf = w[f];
+        const double pf = __dadd_rn(__dmul_rn(wf, p[l[f]]), __dmul_rn(__dsub_rn(1.0, wf), p[u[f]]));
+        const double* s = sf + 3 * (size_t)f;
+        t[f] = make_double4(__dmul_rn(s[0], pf), __dmul_rn(s[1], pf), __dmul_rn(s[2], pf), 0.0);
+    }
+}
+
+// one 32-byte face record of the gradient's face pass, evict-first
+__device__ __forceinline__ double4 ld_t4(const double4* t, int f)
+{
+    const double2* q = reinterpret_cast<const double2*>(t + f);
+    const double2 a = __ldcs(q), b = __ldcs(q + 1);
+    return make_double4(a.x, a.y, b.x, b.y);
+}
+
+__global__ void __launch_bounds__(256, 8) k_fv_grad_cell(int n, const int* __restrict__ lo_start,
+                                                         const int* __restrict__ lo_face,
+                                                         const int* __restrict__ own_start,
+                                                         const double4* __restrict__ t, const double* __restrict__ p,
+                                                         const int* __restrict__ bstart, const int* __restrict__ blist,
+                                                         const double* __restrict__ bsf,
+                                                         const int8_t* __restrict__ btype,
+                                                         const double* __restrict__ v, double* __restrict__ grad)
 {
     constexpr int G = 4;   // faces whose loads are issued together
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double g[3] = {0.0, 0.0, 0.0};
-        const double pi = p[i];
+        double gx = 0.0, gy = 0.0, gz = 0.0;
         const int k1 = lo_start[i + 1];
-        for (int k0 = lo_start[i]; k0 < k1; k0 += G) {   // i = u(f)
-            int f[G];
-            double wf[G], po[G], s[G][3];
+        for (int k0 = lo_start[i]; k0 < k1; k0 += G) {   // i = u(f): -t_f
+            double4 tv[G];
 #pragma unroll
-            for (int j = 0; j < G; j++) f[j] = k0 + j < k1 ? lo_face[k0 + j] : -1;
-#pragma unroll
-            for (int j = 0; j < G; j++) {
-                const bool ok = f[j] >= 0;
-                wf[j] = ok ? w[f[j]] : 0.0;
-                po[j] = ok ? p[l[f[j]]] : 0.0;
-#pragma unroll
-                for (int d = 0; d < 3; d++) s[j][d] = ok ? sf[3 * (size_t)f[j] + d] : 0.0;
-            }
+            for (int j = 0; j < G; j++) tv[j] = k0 + j < k1 ? ld_t4(t, lo_face[k0 + j]) : make_double4(0, 0, 0, 0);
 #pragma unroll
             for (int j = 0; j < G; j++)
-                if (f[j] >= 0) {
-                    const double pf = __dadd_rn(__dmul_rn(wf[j], po[j]), __dmul_rn(__dsub_rn(1.0, wf[j]), pi));
-#pragma unroll
-                    for (int d = 0; d < 3; d++) g[d] = __dsub_rn(g[d], __dmul_rn(s[j][d], pf));
+                if (k0 + j < k1) {
+                    gx = __dsub_rn(gx, tv[j].x);
+                    gy = __dsub_rn(gy, tv[j].y);
+                    gz = __dsub_rn(gz, tv[j].z);
                 }
         }
         const int f1 = own_start[i + 1];
-        for (int f0 = own_start[i]; f0 < f1; f0 += G) {  // i = l(f)
-            double wf[G], po[G], s[G][3];
+        for (int f0 = own_start[i]; f0 < f1; f0 += G) {  // i = l(f): +t_f
+            double4 tv[G];
 #pragma unroll
-            for (int j = 0; j < G; j++) {
-                const int f = f0 + j;
-                const bool ok = f < f1;
-                wf[j] = ok ? w[f] : 0.0;
-                po[j] = ok ? p[u[f]] : 0.0;
-#pragma unroll
-                for (int d = 0; d < 3; d++) s[j][d] = ok ? sf[3 * (size_t)f + d] : 0.0;
-            }
+            for (int j = 0; j < G; j++) tv[j] = f0 + j < f1 ? ld_t4(t, f0 + j) : make_double4(0, 0, 0, 0);
 #pragma unroll
             for (int j = 0; j < G; j++)
                 if (f0 + j < f1) {
-                    const double pf = __dadd_rn(__dmul_rn(wf[j], pi), __dmul_rn(__dsub_rn(1.0, wf[j]), po[j]));
-#pragma unroll
-                    for (int d = 0; d < 3; d++) g[d] = __dadd_rn(g[d], __dmul_rn(s[j][d], pf));
+                    gx = __dadd_rn(gx, tv[j].x);
+                    gy = __dadd_rn(gy, tv[j].y);
+                    gz = __dadd_rn(gz, tv[j].z);
                 }
         }
         if (bstart) {
+            const double pi = p[i];
             for (int k = bstart[i]; k < bstart[i + 1]; k++) {
                 const int b = blist[k];
                 const double pb = btype[b] == 1 ? 0.0 : pi;
-#pragma unroll
-                for (int d = 0; d < 3; d++) g[d] = __dadd_rn(g[d], __dmul_rn(bsf[3 * (size_t)b + d], pb));
+                gx = __dadd_rn(gx, __dmul_rn(bsf[3 * (size_t)b + 0], pb));
+                gy = __dadd_rn(gy, __dmul_rn(bsf[3 * (size_t)b + 1], pb));
+                gz = __dadd_rn(gz, __dmul_rn(bsf[3 * (size_t)b + 2], pb));
             }
         }
         const double vi = v[i];
-#pragma unroll
-        for (int d = 0; d < 3; d++) grad[3 * (size_t)i + d] = __ddiv_rn(g[d], vi);
+        grad[3 * (size_t)i + 0] = __ddiv_rn(gx, vi);
+        grad[3 * (size_t)i + 1] = __ddiv_rn(gy, vi);
+        grad[3 * (size_t)i + 2] = __ddiv_rn(gz, vi);
     }
 }
 
 // Explicit non-orthogonal correction flux of the corrected laplacian:
 // corr_f = (gamma_f |S|) (k . (w grad_l + (1 - w) grad_u)), k = S/|S| - d delta,
 // delta = 1/max(n.d, 0.05 |d|) (the implicit part's coefficient).
+// dcp_f = corr_f - phi_f as well, the face term of the right-hand side.
 __global__ void k_fv_corr(int nf, const int* __restrict__ l, const int* __restrict__ u,
                           const double* __restrict__ sf, const double* __restrict__ c,
                           const double* __restrict__ w, const double* __restrict__ gamma,
-                          const double* __restrict__ grad, double* __restrict__ corr)
+                          const double* __restrict__ grad, const double* __restrict__ phi, double* __restrict__ corr,
+                          double* __restrict__ dcp)
 {
     for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gridDim.x * blockDim.x) {
         const double* s = sf + 3 * (size_t)f;
@@ -172,56 +188,57 @@ __global__ void k_fv_corr(int nf, const int* __restrict__ l, const int* __restri
         const double gx = __dadd_rn(__dmul_rn(wf, gl[0]), __dmul_rn(wu, gu[0]));
         const double gy = __dadd_rn(__dmul_rn(wf, gl[1]), __dmul_rn(wu, gu[1]));
         const double gz = __dadd_rn(__dmul_rn(wf, gl[2]), __dmul_rn(wu, gu[2]));
-        corr[f] = __dmul_rn(__dmul_rn(gamma[f], mags),
-                            __dadd_rn(__dadd_rn(__dmul_rn(kx, gx), __dmul_rn(ky, gy)), __dmul_rn(kz, gz)));
+        const double cf = __dmul_rn(__dmul_rn(gamma[f], mags),
+                                    __dadd_rn(__dadd_rn(__dmul_rn(kx, gx), __dmul_rn(ky, gy)), __dmul_rn(kz, gz)));
+        corr[f] = cf;
+        dcp[f] = __dsub_rn(cf, phi[f]);
     }
 }
 
-// b_i = sum over the faces of i of +-(corr_f - phi_f) (+ owner, - neighbour),
-// then minus the boundary fluxes of i: A p = b for laplacian(gamma, p) =
-// div(phiHbyA) with A = -(implicit laplacian).  With corr = NULL: the
-// integrated divergence sum +-phi_f + boundary fluxes instead.
-__global__ void k_fv_cell_sum(int n, const int* __restrict__ lo_start, const int* __restrict__ lo_face,
-                              const int* __restrict__ own_start, const double* __restrict__ corr,
-                              const double* __restrict__ phi, const int* __restrict__ bstart,
-                              const int* __restrict__ blist, const double* __restrict__ bphi, double* __restrict__ out)
+// out_i = sum over the faces of i of -val_f (neighbour side) and +val_f
+// (owner side), ascending face order, then over its boundary faces of
+// bsign bphi_b.  Right-hand side: val = corr - phi, bsign = -1 (A p = b for
+// laplacian(gamma, p) = div(phiHbyA), A = -(implicit laplacian)); integrated
+// divergence: val = phi, bsign = +1.  All loads of a group of faces are
+// issued together, the sums taken in order.
+__global__ void __launch_bounds__(256, 8) k_fv_cell_sum(int n, const int* __restrict__ lo_start,
+                                                        const int* __restrict__ lo_face,
+                                                        const int* __restrict__ own_start,
+                                                        const double* __restrict__ val,
+                                                        const int* __restrict__ bstart, const int* __restrict__ blist,
+                                                        const double* __restrict__ bphi, int bsign,
+                                                        double* __restrict__ out)
 {
-    constexpr int G = 4;
+    constexpr int G = 6;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int k0 = lo_start[i], k1 = lo_start[i + 1], f0 = own_start[i], f1 = own_start[i + 1];
         double acc = 0.0;
-        const int k1 = lo_start[i + 1], f1 = own_start[i + 1];
-        // neighbour-side faces subtract, owner-side faces add; with corr the
-        // face term is corr_f - phi_f, else phi_f; loads issued G at a time
-        for (int k0 = lo_start[i]; k0 < k1; k0 += G) {
+        for (int kb = k0; kb < k1; kb += G) {
             int f[G];
+#pragma unroll
+            for (int j = 0; j < G; j++) f[j] = kb + j < k1 ? __ldcs(lo_face + kb + j) : -1;
             double t[G];
 #pragma unroll
-            for (int j = 0; j < G; j++) f[j] = k0 + j < k1 ? lo_face[k0 + j] : -1;
-#pragma unroll
-            for (int j = 0; j < G; j++)
-                t[j] = f[j] < 0 ? 0.0 : (corr ? __dsub_rn(corr[f[j]], phi[f[j]]) : phi[f[j]]);
+            for (int j = 0; j < G; j++) t[j] = f[j] >= 0 ? __ldcs(val + f[j]) : 0.0;
 #pragma unroll
             for (int j = 0; j < G; j++)
                 if (f[j] >= 0) acc = __dsub_rn(acc, t[j]);
         }
-        for (int f0 = own_start[i]; f0 < f1; f0 += G) {
+        for (int fb = f0; fb < f1; fb += G) {
             double t[G];
 #pragma unroll
-            for (int j = 0; j < G; j++) {
-                const int f = f0 + j;
-                t[j] = f >= f1 ? 0.0 : (corr ? __dsub_rn(corr[f], phi[f]) : phi[f]);
-            }
+            for (int j = 0; j < G; j++) t[j] = fb + j < f1 ? __ldcs(val + fb + j) : 0.0;
 #pragma unroll
             for (int j = 0; j < G; j++)
-                if (f0 + j < f1) acc = __dadd_rn(acc, t[j]);
+                if (fb + j < f1) acc = __dadd_rn(acc, t[j]);
         }
         if (bstart) {
-            if (corr)
+            if (bsign < 0)
                 for (int k = bstart[i]; k < bstart[i + 1]; k++) acc = __dsub_rn(acc, bphi[blist[k]]);
             else
                 for (int k = bstart[i]; k < bstart[i + 1]; k++) acc = __dadd_rn(acc, bphi[blist[k]]);
         }
-        out[i] = acc;
+        __stcs(out + i, acc);
     }
 }
 
@@ -256,8 +273,10 @@ __global__ void k_fv_bflux(int nb, const int* __restrict__ bcell, const int8_t* 
     }
 }
 
-// Builds the per-cell boundary lists in the handle's (idle) vector region:
-// bstart[n+1] in x64, blist[nb] from p64 on.
+// Per-cell boundary lists: bstart[n+1], blist[nb].  Built once per boundary
+// (bface_cell pointer and count) into the handle's boundary region and reused
+// by later calls; a boundary with more than 2 faces per cell on average is
+// built on every call into the (idle) vector region instead.
 static spuma_status boundary_lists(spuma_ldu_t h, int nb, const int* bcell, int** bstart_out, int** blist_out,
                                    cudaStream_t s)
 {
@@ -269,11 +288,15 @@ static spuma_status boundary_lists(spuma_ldu_t h, int nb, const int* bcell, int*
         return SPUMA_ERR_WORKSPACE_TOO_SMALL;
     }
     const Layout& L = h->L;
+    const bool cached = (size_t)nb <= L.blist_cap;
+    int* bstart = cached ? h->at<int>(L.bstart) : h->at<int>(L.x64);
+    int* blist = cached ? h->at<int>(L.blist) : h->at<int>(L.p64);
+    *bstart_out = bstart;
+    *blist_out = blist;
+    if (cached && h->bl_cell == bcell && h->bl_nb == nb) return SPUMA_OK;
     const int T = 256;
-    int* bstart = h->at<int>(L.x64);
     int* cursor = h->at<int>(L.r64);
     int* tmp = h->at<int>(L.w64);
-    int* blist = h->at<int>(L.p64);
     SPUMA_CUDA(cudaMemsetAsync(bstart, 0, 4 * (size_t)(h->n + 1), s));
     k_fv_bcount<<<grid_fv(nb, T, h->num_sms), T, 0, s>>>(nb, bcell, bstart);
     count_launch();
@@ -283,9 +306,21 @@ static spuma_status boundary_lists(spuma_ldu_t h, int nb, const int* bcell, int*
     k_fv_bfill<<<grid_fv(nb, T, h->num_sms), T, 0, s>>>(nb, bcell, cursor, blist);
     k_fv_bsort<<<grid_fv(h->n, T, h->num_sms), T, 0, s>>>(h->n, bstart, blist);
     count_launch(2);
-    *bstart_out = bstart;
-    *blist_out = blist;
+    SPUMA_CUDA(cudaGetLastError());
+    if (cached) {
+        h->bl_cell = bcell;
+        h->bl_nb = nb;
+    }
     return SPUMA_OK;
+}
+
+// Face-indexed scratch of the operators: the matrix region (La64 .. Uc64,
+// 32F bytes at least); a matrix prepared with spuma_matrix_prepare() is no
+// longer valid afterwards.
+static char* face_scratch(spuma_ldu_t h)
+{
+    h->prepared_precond = -1;
+    return h->at<char>(h->L.La64);
 }
 
 }  // namespace spuma
@@ -325,9 +360,15 @@ spuma_status spuma_fv_grad(spuma_ldu_t h, const double* face_sf, const double* w
     spuma_status st = boundary_lists(h, n_bfaces, bface_cell, &bstart, &blist, s);
     if (st != SPUMA_OK) return st;
     const Layout& L = h->L;
-    k_fv_grad<<<grid_fv(h->n, 256, h->num_sms), 256, 0, s>>>(
-        h->n, h->at<int>(L.lo_start), h->at<int>(L.lo_face), h->at<int>(L.own_start), h->at<int>(L.laddr),
-        h->at<int>(L.uaddr), face_sf, w, p, bstart, blist, bface_sf, bface_type, cell_v, grad);
+    double4* t = reinterpret_cast<double4*>(face_scratch(h));
+    if (h->nf > 0) {
+        k_fv_grad_face<<<std::min(grid_fv(h->nf, 256, h->num_sms), h->num_sms * 8), 256, 0, s>>>(
+            h->nf, h->at<int>(L.laddr), h->at<int>(L.uaddr), face_sf, w, p, t);
+        count_launch();
+    }
+    k_fv_grad_cell<<<std::min(grid_fv(h->n, 256, h->num_sms), h->num_sms * 8), 256, 0, s>>>(
+        h->n, h->at<int>(L.lo_start), h->at<int>(L.lo_face), h->at<int>(L.own_start), t, p, bstart, blist, bface_sf,
+        bface_type, cell_v, grad);
     count_launch();
     SPUMA_CUDA(cudaGetLastError());
     return SPUMA_OK;
@@ -346,17 +387,18 @@ spuma_status spuma_pressure_rhs(spuma_ldu_t h, const double* face_sf, const doub
     if (h->n == 0) return SPUMA_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const Layout& L = h->L;
+    double* dcp = reinterpret_cast<double*>(face_scratch(h));
     if (h->nf > 0) {
         k_fv_corr<<<grid_fv(h->nf, 256, h->num_sms), 256, 0, s>>>(h->nf, h->at<int>(L.laddr), h->at<int>(L.uaddr),
-                                                                  face_sf, cell_c, w, face_gamma, grad, corr);
+                                                                  face_sf, cell_c, w, face_gamma, grad, phi, corr,
+                                                                  dcp);
         count_launch();
     }
     int *bstart, *blist;
     spuma_status st = boundary_lists(h, n_bfaces, bface_cell, &bstart, &blist, s);
     if (st != SPUMA_OK) return st;
-    k_fv_cell_sum<<<grid_fv(h->n, 256, h->num_sms), 256, 0, s>>>(h->n, h->at<int>(L.lo_start), h->at<int>(L.lo_face),
-                                                                 h->at<int>(L.own_start), corr, phi, bstart, blist,
-                                                                 bphi, b);
+    k_fv_cell_sum<<<std::min(grid_fv(h->n, 256, h->num_sms), h->num_sms * 8), 256, 0, s>>>(
+        h->n, h->at<int>(L.lo_start), h->at<int>(L.lo_face), h->at<int>(L.own_start), dcp, bstart, blist, bphi, -1, b);
     count_launch();
     SPUMA_CUDA(cudaGetLastError());
     return SPUMA_OK;
@@ -403,9 +445,8 @@ spuma_status spuma_fv_div(spuma_ldu_t h, const double* phi, int32_t n_bfaces, co
     spuma_status st = boundary_lists(h, n_bfaces, bface_cell, &bstart, &blist, s);
     if (st != SPUMA_OK) return st;
     const Layout& L = h->L;
-    k_fv_cell_sum<<<grid_fv(h->n, 256, h->num_sms), 256, 0, s>>>(h->n, h->at<int>(L.lo_start), h->at<int>(L.lo_face),
-                                                                 h->at<int>(L.own_start), nullptr, phi, bstart, blist,
-                                                                 bphi, div);
+    k_fv_cell_sum<<<std::min(grid_fv(h->n, 256, h->num_sms), h->num_sms * 8), 256, 0, s>>>(
+        h->n, h->at<int>(L.lo_start), h->at<int>(L.lo_face), h->at<int>(L.own_start), phi, bstart, blist, bphi, 1, div);
     count_launch();
     SPUMA_CUDA(cudaGetLastError());
     return SPUMA_OK;

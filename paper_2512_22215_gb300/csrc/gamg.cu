@@ -1,7 +1,8 @@
 // gamg.cu -- GAMG for the pressure equation (the paper's production pressure
 // solver: "GAMG, smoother Richardson", Richardson on every level and a
 // diagonal-preconditioned PCG at the coarsest one, with OpenFOAM's coarsening
-// unmodified).
+// unmodified; the paper's other options, Sec. 4.3 smoother table: the
+// two-stage Gauss-Seidel smoother and DIC-PCG at the coarsest level).
 //
 // The hierarchy depends on the mesh only (faces and their area weights), so
 // it is built once, on the host, when the solver object is created, as
@@ -20,7 +21,8 @@
 // normalised residual and stopping rule.  V(k, r): no pre-smoothing;
 // restriction (sum over the aggregate); the coarsest level by diagonal PCG
 // from 0 to 1e-8 relative; prolongation by injection, scaled by the A-norm
-// optimal step (e.r)/(e.Ae); two damped-Jacobi sweeps e += (2/3 rD)(r - Ae).
+// optimal step (e.r)/(e.Ae); two damped-Jacobi sweeps e += (2/3 rD)(r - Ae)
+// (or two two-stage Gauss-Seidel sweeps e += (D^-1 - D^-1 L D^-1)(r - A e)).
 // Levels of at most two rows per thread of one block run on the first block
 // alone with block-level barriers; the others on the whole grid.  Every
 // per-row sum follows the sequential definition's order; dot products are
@@ -51,9 +53,9 @@ struct GamgLevel {
     const int *iptr, *iface;                // next-level cell -> the faces inside it (ascending)
     const double *diag, *upper;             // A_k (level 0: the caller's arrays)
     double *cdiag, *cupper;                 // A_{k+1} written here (k < L-1)
-    double *wrd;                            // omega / diag
+    double *wrd;                            // omega / diag (Richardson) or 1 / diag (two-stage Gauss-Seidel)
     double *rval;                           // A_k's off-diagonal coefficients in row-CSR order (per solve)
-    double *r, *e, *q;                      // right-hand side, correction, scratch
+    double *r, *e, *q, *y;                  // right-hand side, correction, scratch, first-stage vector
 };
 
 struct GamgArgs {
@@ -63,6 +65,9 @@ struct GamgArgs {
     double* x_orig;
     double *x, *b, *res;                    // level-0 solution, rhs, outer residual (= lv[0].r)
     double *pw, *pp, *pq, *px;              // coarsest-level PCG vectors
+    double* crD;                            // coarsest-level DIC reciprocal pivots
+    int smoother;                           // 0 Richardson, 1 two-stage Gauss-Seidel
+    int coarsest_precond;                   // SPUMA_PRECOND_DIAGONAL or SPUMA_PRECOND_DIC
     double* partials;
     int* status;
     spuma_solver_perf* perf;
@@ -162,10 +167,54 @@ __device__ bool gamg_coarse_matrices(const GamgArgs& a, const Group& g)
     const int first = g.bid * (int)blockDim.x + (int)threadIdx.x, stride = g.nblocks * (int)blockDim.x;
     for (int k = 0; k < a.nlev; k++) {
         const GamgLevel& L = a.lv[k];
-        for (int i = first; i < L.n; i += stride) L.wrd[i] = __dmul_rn(kGamgOmega, __ddiv_rn(1.0, L.diag[i]));
+        for (int i = first; i < L.n; i += stride)
+            L.wrd[i] = a.smoother == 1 ? __ddiv_rn(1.0, L.diag[i]) : __dmul_rn(kGamgOmega, __ddiv_rn(1.0, L.diag[i]));
         for (int e = first; e < 2 * L.nf; e += stride) L.rval[e] = L.upper[L.rfac[e]];
     }
+    if (!group_sync(g)) return false;
+    // DIC factor of the coarsest matrix by one thread, rows ascending: p_i =
+    // d_i - sum of (a a)/p_col over the row's lower entries in face order (the
+    // sequential face loop's order), then rD = 1/p; a pivot <= 0 is an error
+    if (a.coarsest_precond == SPUMA_PRECOND_DIC && g.bid == 0 && threadIdx.x == 0) {
+        const GamgLevel& L = a.lv[a.nlev - 1];
+        for (int i = 0; i < L.n; i++) {
+            double piv = L.diag[i];
+            for (int e = L.rptr[i]; e < L.rptr[i + 1]; e++) {
+                const int c = L.rcol[e];
+                if (c < i) piv = __dsub_rn(piv, __ddiv_rn(__dmul_rn(L.rval[e], L.rval[e]), a.crD[c]));
+            }
+            a.crD[i] = piv;
+            if (!(piv > 0.0)) flag_error(a.status, SPUMA_ERR_NOT_SPD, i);
+        }
+        for (int i = 0; i < L.n; i++) a.crD[i] = __ddiv_rn(1.0, a.crD[i]);
+    }
     return group_sync(g);
+}
+
+// w = M^-1 r for the coarsest level's DIC factor, by one thread: w_i = rD_i
+// r_i; forward, rows ascending, lower entries in face order: w_i -= (rD_i a)
+// w_col; backward, rows descending, upper entries in descending face order:
+// w_i -= (rD_i a) w_col; each -= one FMA of the rounded product (the order of
+// the sequential face loops).
+__device__ void gamg_dic_seq(const GamgLevel& L, const double* rD, const double* r, double* w)
+{
+    for (int i = 0; i < L.n; i++) w[i] = __dmul_rn(rD[i], r[i]);
+    for (int i = 0; i < L.n; i++) {
+        double wi = w[i];
+        for (int e = L.rptr[i]; e < L.rptr[i + 1]; e++) {
+            const int c = L.rcol[e];
+            if (c < i) wi = __fma_rn(-__dmul_rn(rD[i], L.rval[e]), w[c], wi);
+        }
+        w[i] = wi;
+    }
+    for (int i = L.n - 1; i >= 0; i--) {
+        double wi = w[i];
+        for (int e = L.rptr[i + 1] - 1; e >= L.rptr[i]; e--) {
+            const int c = L.rcol[e];
+            if (c > i) wi = __fma_rn(-__dmul_rn(rD[i], L.rval[e]), w[c], wi);
+        }
+        w[i] = wi;
+    }
 }
 
 // Coarsest level: PCG with the diagonal preconditioner from 0, relative
@@ -196,12 +245,17 @@ __device__ bool gamg_coarsest(const GamgArgs& a, const Group& g)
         do {
             rho_old = rho;
             double t[1] = {0.0};
-            if (x.active)
+            if (a.coarsest_precond == SPUMA_PRECOND_DIC) {
+                if (g.bid == 0 && threadIdx.x == 0) gamg_dic_seq(L, a.crD, r, w);
+                if (!exec_sync(x, g)) return false;
+                for (int i = x.first; i < L.n; i += x.stride) t[0] = __fma_rn(w[i], r[i], t[0]);
+            } else {
                 for (int i = x.first; i < L.n; i += x.stride) {
                     const double wi = __dmul_rn(__ddiv_rn(1.0, L.diag[i]), r[i]);
                     w[i] = wi;
                     t[0] = __fma_rn(wi, r[i], t[0]);
                 }
+            }
             if (!exec_sum<1>(x, t, a, GS_B, g)) return false;
             rho = t[0];
             const double beta = it == 0 ? 0.0 : rho / rho_old;
@@ -272,15 +326,39 @@ __device__ bool gamg_vcycle(const GamgArgs& a, const Group& g)
                 for (int i = x.first; i < L.n; i += x.stride) L.e[i] = __dmul_rn(L.e[i], sc);
             if (!exec_sync(x, g)) return false;
         }
-        // Jacobi sweeps alternate between e and q (an even count ends in e)
-        static_assert(kGamgPostSweeps % 2 == 0, "sweeps alternate e -> q -> e");
-        for (int s = 0; s < kGamgPostSweeps; s++) {
-            const double* src = (s & 1) ? L.q : L.e;
-            double* dst = (s & 1) ? L.e : L.q;
-            if (x.active)
-                for (int i = x.first; i < L.n; i += x.stride)
-                    dst[i] = __fma_rn(L.wrd[i], __dsub_rn(L.r[i], gamg_amul_row(L, L.diag, src, i)), src[i]);
-            if (!exec_sync(x, g)) return false;
+        if (a.smoother == 1) {
+            // two-stage Gauss-Seidel: q = r - A e, y = rD q; then e += rD (q - L y),
+            // the row's lower entries in face order (one FMA each)
+            for (int s = 0; s < kGamgPostSweeps; s++) {
+                if (x.active)
+                    for (int i = x.first; i < L.n; i += x.stride) {
+                        const double qi = __dsub_rn(L.r[i], gamg_amul_row(L, L.diag, L.e, i));
+                        L.q[i] = qi;
+                        L.y[i] = __dmul_rn(L.wrd[i], qi);
+                    }
+                if (!exec_sync(x, g)) return false;
+                if (x.active)
+                    for (int i = x.first; i < L.n; i += x.stride) {
+                        double si = L.q[i];
+                        for (int e = L.rptr[i]; e < L.rptr[i + 1]; e++) {
+                            const int c = L.rcol[e];
+                            if (c < i) si = __fma_rn(-L.rval[e], L.y[c], si);
+                        }
+                        L.e[i] = __dadd_rn(L.e[i], __dmul_rn(L.wrd[i], si));
+                    }
+                if (!exec_sync(x, g)) return false;
+            }
+        } else {
+            // Jacobi sweeps alternate between e and q (an even count ends in e)
+            static_assert(kGamgPostSweeps % 2 == 0, "sweeps alternate e -> q -> e");
+            for (int s = 0; s < kGamgPostSweeps; s++) {
+                const double* src = (s & 1) ? L.q : L.e;
+                double* dst = (s & 1) ? L.e : L.q;
+                if (x.active)
+                    for (int i = x.first; i < L.n; i += x.stride)
+                        dst[i] = __fma_rn(L.wrd[i], __dsub_rn(L.r[i], gamg_amul_row(L, L.diag, src, i)), src[i]);
+                if (!exec_sync(x, g)) return false;
+            }
         }
     }
     if (a.nlev == 1 || a.small_from == 0) return group_sync(g);
@@ -462,8 +540,11 @@ struct spuma_gamg {
     GamgLevel* dlv = nullptr;            // device descriptors
     std::vector<GamgLevel> hlv;          // host copy of the descriptors
     double *x = nullptr, *b = nullptr, *pw = nullptr, *pp = nullptr, *pq = nullptr, *px = nullptr;
+    double* crD = nullptr;
     double* partials = nullptr;
     int small_from = 0;
+    int smoother = 0;                      // 0 Richardson, 1 two-stage Gauss-Seidel
+    int coarsest_precond = SPUMA_PRECOND_DIAGONAL;
 };
 
 namespace {
@@ -505,6 +586,7 @@ size_t gamg_layout(spuma_gamg& G, bool assign)
         D.r = (double*)take(8 * (size_t)H.n + 8);
         D.e = (double*)take(8 * (size_t)H.n + 8);
         D.q = (double*)take(8 * (size_t)H.n + 8);
+        D.y = (double*)take(8 * (size_t)H.n + 8);
     }
     for (int k = 0; k + 1 < L; k++) {
         G.hlv[k].cdiag = const_cast<double*>(G.hlv[k + 1].diag);
@@ -517,6 +599,7 @@ size_t gamg_layout(spuma_gamg& G, bool assign)
     G.pp = (double*)take(8 * nc + 8);
     G.pq = (double*)take(8 * nc + 8);
     G.px = (double*)take(8 * nc + 8);
+    G.crD = (double*)take(8 * nc + 8);
     G.partials = (double*)take(8 * (size_t)kMaxBlocks * kSlots);
     return off;
 }
@@ -701,6 +784,9 @@ spuma_status spuma_gamg_solve(spuma_gamg_t g, const double* diag, const double* 
     a.pp = g->pp;
     a.pq = g->pq;
     a.px = g->px;
+    a.crD = g->crD;
+    a.smoother = g->smoother;
+    a.coarsest_precond = g->coarsest_precond;
     a.partials = g->partials;
     a.status = h->at<int>(h->L.status);
     a.perf = perf;
@@ -719,6 +805,18 @@ spuma_status spuma_gamg_solve(spuma_gamg_t g, const double* diag, const double* 
     void* args[] = {(void*)&a, (void*)&tns};
     SPUMA_CUDA(cudaLaunchCooperativeKernel((const void*)k_gamg, grid, 1024, args, 0, s));
     count_launch();
+    return SPUMA_OK;
+}
+
+spuma_status spuma_gamg_set_options(spuma_gamg_t g, int32_t smoother, int32_t coarsest_precond)
+{
+    if (!g || (smoother != SPUMA_GAMG_RICHARDSON && smoother != SPUMA_GAMG_GAUSS_SEIDEL_2STAGE) ||
+        (coarsest_precond != SPUMA_PRECOND_DIAGONAL && coarsest_precond != SPUMA_PRECOND_DIC)) {
+        set_error("spuma_gamg_set_options: bad argument (smoother 0 or 1, coarsest preconditioner DIAGONAL or DIC)");
+        return SPUMA_ERR_INVALID_ARG;
+    }
+    g->smoother = smoother;
+    g->coarsest_precond = coarsest_precond;
     return SPUMA_OK;
 }
 

@@ -570,8 +570,6 @@ __device__ bool phase_factor(const SolveArgs& a, const Group& g)
             }
         }
     }
-    // the staged sweeps read rD and the sweep coefficients with bulk copies
-    if (a.stage) fence_proxy_async_global();
     return group_sync(g);
 }
 
@@ -703,313 +701,6 @@ __device__ bool dic_apply(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const 
         if (!end_step(L == 0)) return false;
         pc.lap(CK_BWD + min(L, 63));
     }
-    return true;
-}
-
-// ------------------------------------------------ staged DIC sweeps ------
-// The sweeps' matrix rows (row extents, columns, coefficients and, forward,
-// rD) do not change during a solve, so their loads need not wait for the
-// previous level.  Each block takes one contiguous chunk of every level's
-// rows, cut into pieces of StageCfg::RP rows, and its first thread streams
-// the pieces into a two-stage ring in shared memory with 1-D bulk copies
-// (completion counted in bytes on one mbarrier per stage), two pieces ahead
-// of the rows being swept; the next level's first pieces are copied while the
-// grid barrier after a level waits.  A row's remaining global loads are the
-// gathers of w and its own r (forward) or w and r (backward).  A piece whose
-// entries exceed the ring's room reads them from global memory (its extents
-// are still staged).  Pieces are enumerated forward levels 0 .. tail-1, then
-// backward levels from the highest swept one down to 0; the block's running
-// count of consumed pieces gives the stage (count & 1) and the mbarrier's
-// phase parity ((count >> 1) & 1).  Every wait is bounded: a wait that runs
-// out records SPUMA_ERR_DEVICE_TIMEOUT, skips the piece's rows, and the group
-// stops at its next grid barrier after the first thread has waited (again
-// bounded) for the copies it issued.
-template <class T>
-struct StageCfg {
-    static constexpr int RP = sizeof(T) == 4 ? 2048 : 1024;   // rows per piece
-    static constexpr int EC = RP * 11 / 2;                     // entries per piece (5.5 per row)
-    static constexpr int V = 16 / (int)sizeof(T);              // elements per 16 bytes
-    static constexpr size_t PTR = 0;
-    static constexpr size_t RDO = PTR + (size_t)(RP + 8) * 4;
-    static constexpr size_t COL = RDO + (size_t)(RP + 8) * sizeof(T);
-    static constexpr size_t COEF = COL + (size_t)(EC + 8) * 4;
-    static constexpr size_t STAGE = (COEF + (size_t)(EC + 8) * sizeof(T) + 127) / 128 * 128;
-    static constexpr size_t BYTES = 2 * STAGE;
-    static_assert(RDO % 16 == 0 && COL % 16 == 0 && COEF % 16 == 0, "16-byte aligned regions");
-};
-
-struct StageRing {
-    unsigned long long bar[2];   // one mbarrier per stage
-    unsigned consumed;           // pieces this block has consumed (block-uniform)
-};
-__shared__ StageRing g_ring;
-extern __shared__ __align__(128) unsigned char g_dsmem[];
-
-// Once per launch, before the first staged sweep (all threads call it).
-__device__ __forceinline__ void stage_ring_init()
-{
-    if (threadIdx.x == 0) {
-        mbar_init(&g_ring.bar[0], 1);
-        mbar_init(&g_ring.bar[1], 1);
-        fence_mbar_init();
-        g_ring.consumed = 0;
-    }
-    __syncthreads();
-}
-
-__device__ __forceinline__ bool ring_wait(unsigned long long* bar, unsigned parity, unsigned long long timeout_ns)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_timer_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (global_timer_ns() - t0 > timeout_ns) return false;
-    return true;
-}
-
-// The block's contiguous chunk [c0, c1) of level L.
-__device__ __forceinline__ void level_chunk(const int* lvl, int L, const Group& g, int& c0, int& c1)
-{
-    const int r0 = lvl[L], r1 = lvl[L + 1];
-    const int chunk = (r1 - r0 + g.nblocks - 1) / g.nblocks;
-    c0 = (int)min((long long)r0 + (long long)g.bid * chunk, (long long)r1);
-    c1 = min(c0 + chunk, r1);
-}
-
-// The issuing thread's walk over the pieces (the consumers' loops visit the
-// same pieces in the same order).
-struct PieceCursor {
-    int dir;      // 0 forward, 1 backward, 2 done
-    int L, row0, c1;
-};
-
-template <class T>
-__device__ __forceinline__ void cursor_level(PieceCursor& c, const SolveArgs& a, const Group& g, int tail)
-{
-    // from (dir, L): first level at or after it that has rows of this block
-    for (;;) {
-        if (c.dir == 0 && c.L >= tail) {
-            c.dir = 1;
-            c.L = min(tail, a.nlev - 1) - 1;
-        }
-        if (c.dir == 1 && c.L < 0) c.dir = 2;
-        if (c.dir == 2) return;
-        int c0;
-        level_chunk(a.lvl, c.L, g, c0, c.c1);
-        c.row0 = c0;
-        if (c0 < c.c1) return;
-        c.L += c.dir == 0 ? 1 : -1;
-    }
-}
-
-template <class T>
-__device__ __forceinline__ void cursor_next(PieceCursor& c, const SolveArgs& a, const Group& g, int tail)
-{
-    c.row0 += StageCfg<T>::RP;
-    if (c.row0 < c.c1) return;
-    c.L += c.dir == 0 ? 1 : -1;
-    cursor_level<T>(c, a, g, tail);
-}
-
-// Copies of one piece: its extents [row0, row1], rD (forward) and, when they
-// fit, its entries; every range rounded out to 16 bytes (inside the arrays'
-// 256-byte padded regions of the workspace).
-template <class T>
-__device__ void issue_piece(const Mat<T>& A, const PieceCursor& c, unsigned long long* bar, unsigned char* buf)
-{
-    using C = StageCfg<T>;
-    const bool fwd = c.dir == 0;
-    const int row0 = c.row0, row1 = min(row0 + C::RP, c.c1);
-    const int* ptr = fwd ? A.Lptr : A.Uptr;
-    const int e0 = ptr[row0], e1 = ptr[row1];
-    const int pa = row0 & ~3, pb = (row1 + 1 + 3) & ~3;
-    unsigned bytes = (unsigned)(pb - pa) * 4u;
-    const int ra = row0 & ~(C::V - 1), rb = (row1 + C::V - 1) & ~(C::V - 1);
-    if (fwd) bytes += (unsigned)(rb - ra) * (unsigned)sizeof(T);
-    const bool ent = e1 > e0 && e1 - e0 <= C::EC;
-    const int ca = e0 & ~3, cb = (e1 + 3) & ~3;
-    const int fa = e0 & ~(C::V - 1), fb = (e1 + C::V - 1) & ~(C::V - 1);
-    if (ent) bytes += (unsigned)(cb - ca) * 4u + (unsigned)(fb - fa) * (unsigned)sizeof(T);
-    mbar_arrive_expect_tx(bar, bytes);
-    bulk_copy_g2s(buf + C::PTR, ptr + pa, (unsigned)(pb - pa) * 4u, bar);
-    if (fwd) bulk_copy_g2s(buf + C::RDO, A.rD + ra, (unsigned)(rb - ra) * (unsigned)sizeof(T), bar);
-    if (ent) {
-        bulk_copy_g2s(buf + C::COL, (fwd ? A.Lcol : A.Ucol) + ca, (unsigned)(cb - ca) * 4u, bar);
-        bulk_copy_g2s(buf + C::COEF, (fwd ? A.Lc : A.Uc) + fa, (unsigned)(fb - fa) * (unsigned)sizeof(T), bar);
-    }
-}
-
-// rows_chain with the entries read from the staged piece (shared memory).
-template <class T, int R, int G, bool DESC>
-__device__ __forceinline__ void rows_chain_staged(T (&acc)[R], const int (&e0)[R], const int (&e1)[R],
-                                                  const int* scol, int ca, const T* scoef, int fa, const T* vec)
-{
-    const unsigned long long pol = keep_policy<T, true>();
-    for (int off = 0;; off += G) {
-        bool more = false;
-#pragma unroll
-        for (int k = 0; k < R; k++) more |= e0[k] + off < e1[k];
-        if (!more) break;
-        int c[R][G];
-        T cf[R][G], v[R][G];
-#pragma unroll
-        for (int k = 0; k < R; k++)
-#pragma unroll
-            for (int j = 0; j < G; j++) {
-                const int ej = DESC ? e1[k] - 1 - off - j : e0[k] + off + j;
-                const bool ok = DESC ? ej >= e0[k] : ej < e1[k];
-                c[k][j] = ok ? scol[ej - ca] : -1;
-                cf[k][j] = ok ? scoef[ej - fa] : T(0);
-            }
-#pragma unroll
-        for (int k = 0; k < R; k++)
-#pragma unroll
-            for (int j = 0; j < G; j++) v[k][j] = c[k][j] >= 0 ? gather<true>(vec, c[k][j], pol) : T(0);
-#pragma unroll
-        for (int k = 0; k < R; k++)
-#pragma unroll
-            for (int j = 0; j < G; j++)
-                if (c[k][j] >= 0) acc[k] = fmadd(-cf[k][j], v[k][j], acc[k]);
-    }
-}
-
-// The rows [row0, row0 + nrows) of one staged piece.  Forward: w = rD r -
-// sum (rD a) w_lower (ascending), with rho terms on the top level; backward:
-// w -= sum (rD a) w_upper (descending), rho += w r.  SENT: entries staged.
-template <class T, bool FWD, bool SENT>
-__device__ __forceinline__ void staged_rows(const Mat<T>& A, Vecs<T> v, int row0, int nrows, const unsigned char* buf,
-                                            int e0p, bool rho, Acc<T>& arho)
-{
-    using C = StageCfg<T>;
-    constexpr int R = ChainShape<T>::R, G = ChainShape<T>::G;
-    const int* sptr = reinterpret_cast<const int*>(buf + C::PTR);
-    const T* srd = reinterpret_cast<const T*>(buf + C::RDO);
-    const int* scol = reinterpret_cast<const int*>(buf + C::COL);
-    const T* scoef = reinterpret_cast<const T*>(buf + C::COEF);
-    const int pa = row0 & ~3, ra = row0 & ~(C::V - 1), ca = e0p & ~3, fa = e0p & ~(C::V - 1);
-    const int bs = (int)blockDim.x;
-    for (int q0 = (int)threadIdx.x; q0 < nrows; q0 += R * bs) {
-        int p[R], e0[R], e1[R];
-        T ww[R], rr[R];
-#pragma unroll
-        for (int k = 0; k < R; k++) {
-            const int q = q0 + k * bs;
-            const bool ok = q < nrows;
-            p[k] = row0 + q;
-            e0[k] = ok ? sptr[p[k] - pa] : 0;
-            e1[k] = ok ? sptr[p[k] + 1 - pa] : 0;
-            rr[k] = ok && (FWD || rho) ? v.r[p[k]] : T(0);
-            if (FWD)
-                ww[k] = ok ? mul_rn(srd[p[k] - ra], rr[k]) : T(0);
-            else
-                ww[k] = ok ? v.w[p[k]] : T(0);
-        }
-        if (SENT)
-            rows_chain_staged<T, R, G, !FWD>(ww, e0, e1, scol, ca, scoef, fa, v.w);
-        else
-            rows_chain<T, R, G, !FWD, true>(ww, e0, e1, FWD ? A.Lcol : A.Ucol, FWD ? A.Lc : A.Uc, v.w);
-#pragma unroll
-        for (int k = 0; k < R; k++)
-            if (q0 + k * bs < nrows) {
-                v.w[p[k]] = ww[k];
-                if (rho) arho.prod(ww[k], rr[k]);
-            }
-    }
-}
-
-// dic_apply with the staged ring (PCG kinds of the single-system solver).
-template <class T>
-__device__ bool dic_apply_staged(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const Group& g, PhaseClock& pc)
-{
-    using C = StageCfg<T>;
-    const int nlev = a.nlev, tail = min(a.tail_from, nlev);
-    const int tid = (int)threadIdx.x, bs = (int)blockDim.x;
-    unsigned cnt = g_ring.consumed, issued = cnt;
-    PieceCursor cur{0, 0, 0, 0};
-    Acc<T> arho;
-    auto issue = [&]() {
-        issue_piece<T>(A, cur, &g_ring.bar[issued & 1], g_dsmem + (issued & 1) * C::STAGE);
-        issued++;
-        cursor_next<T>(cur, a, g, tail);
-    };
-    // copies still in flight when the group stops must land before the block
-    // leaves: the first thread waits for them with a limit of its own (2 s),
-    // independent of the barrier time limit (which a test sets to 0)
-    auto drain = [&]() {
-        if (tid == 0)
-            for (unsigned j = cnt; j < issued; j++) ring_wait(&g_ring.bar[j & 1], (j >> 1) & 1, 2000000000ull);
-        __syncthreads();
-        if (tid == 0) g_ring.consumed = issued;
-    };
-    auto end_step = [&](bool last) {
-        if (last) {
-            double t[1] = {arho.value()};
-            block_reduce_store<1>(t, a.partials, SL_B, g.bid);
-        }
-        return group_sync(g);
-    };
-    if (nlev == 0) return end_step(true);
-    if (tid == 0) {
-        fence_proxy_async_global();
-        cursor_level<T>(cur, a, g, tail);
-        for (int k = 0; k < 2 && cur.dir < 2; k++) issue();
-    }
-    auto consume_level = [&](int L, bool fwd, bool rho) {
-        int c0, c1;
-        level_chunk(a.lvl, L, g, c0, c1);
-        for (int row0 = c0; row0 < c1; row0 += C::RP) {
-            const int nrows = min(C::RP, c1 - row0);
-            const unsigned st = cnt & 1;
-            const unsigned char* buf = g_dsmem + st * C::STAGE;
-            if (ring_wait(&g_ring.bar[st], (cnt >> 1) & 1, g.timeout_ns)) {
-                const int* sptr = reinterpret_cast<const int*>(buf + C::PTR);
-                const int pa = row0 & ~3;
-                const int e0p = sptr[row0 - pa], e1p = sptr[row0 + nrows - pa];
-                const bool sent = e1p > e0p && e1p - e0p <= C::EC;
-                if (fwd) {
-                    if (sent)
-                        staged_rows<T, true, true>(A, v, row0, nrows, buf, e0p, rho, arho);
-                    else
-                        staged_rows<T, true, false>(A, v, row0, nrows, buf, e0p, rho, arho);
-                } else {
-                    if (sent)
-                        staged_rows<T, false, true>(A, v, row0, nrows, buf, e0p, true, arho);
-                    else
-                        staged_rows<T, false, false>(A, v, row0, nrows, buf, e0p, true, arho);
-                }
-            } else {
-                flag_error(a.status, SPUMA_ERR_DEVICE_TIMEOUT, g.bid);
-                if (tid == 0) cur.dir = 2;   // a stage that may still be filling is not refilled
-            }
-            __syncthreads();   // every thread is done with this stage
-            cnt++;
-            if (tid == 0 && cur.dir < 2) issue();
-        }
-    };
-    for (int L = 0; L < tail; L++) {
-        consume_level(L, true, L == nlev - 1);
-        if (!end_step(nlev == 1)) { drain(); return false; }
-        pc.lap(CK_FWD + min(L, 63));
-    }
-    if (tail < nlev) {
-        if (g.bid == 0) {
-            for (int L = tail; L < nlev; L++) {
-                fwd_rows<T, RHO_R>(A, v, a.lvl[L], a.lvl[L + 1], tid, bs, L == nlev - 1, nullptr, arho);
-                __syncthreads();
-            }
-            for (int L = nlev - 2; L >= tail; L--) {
-                bwd_rows<T, RHO_R>(A, v, a.lvl[L], a.lvl[L + 1], tid, bs, nullptr, arho);
-                __syncthreads();
-            }
-        }
-        if (!end_step(tail == 0)) { drain(); return false; }
-        pc.lap(CK_FWD + min(tail, 63));
-    }
-    for (int L = min(tail, nlev - 1) - 1; L >= 0; L--) {
-        consume_level(L, false, true);
-        if (!end_step(L == 0)) { drain(); return false; }
-        pc.lap(CK_BWD + min(L, 63));
-    }
-    if (tid == 0) g_ring.consumed = cnt;
     return true;
 }
 
@@ -1148,7 +839,7 @@ __device__ int precondition(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, bool
             if (act < 0) return -1;
             if (act == 1) return 2;
         }
-        if (!(a.stage ? dic_apply_staged<T>(a, A, v, g, pc) : dic_apply<T>(a, A, v, g, pc))) return -1;
+        if (!dic_apply<T>(a, A, v, g, pc)) return -1;
         double t[1];
         grid_reduce_read<1>(t, a.partials, SL_B, g.nblocks);
         *rho = t[0];
@@ -1538,7 +1229,11 @@ __device__ bool solve_pbicg(const SolveArgs& a, const Group& g, double nfac, dou
 
 enum SolveKind { KIND_SETUP = 0, KIND_F64 = 1, KIND_MIXED = 2, KIND_MIXED_RESTART = 3, KIND_PBICG = 4 };
 
-template <int KIND>
+// TRUE_INLINE: the report's true residual is computed inside the launch
+// (batched launches); the single-system solver leaves it to the two small
+// kernels that follow it on the stream (k_true_residual_*), so that its own
+// register allocation is not burdened by one more Amul.
+template <int KIND, bool TRUE_INLINE>
 __device__ void run_system(const SolveArgs& a, const Group& g)
 {
     spuma_solver_perf pf;
@@ -1601,10 +1296,12 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
                     pf.singular = sing;
                 }
             }
-            if (ok) {
-                Mat<double> A64 = mat_of<double>(a);
-                if (KIND == KIND_PBICG) A64.ell_w = 0;   // asymmetric: the internal CSR holds A
-                ok = true_residual(a, A64, KIND == KIND_PBICG ? nullptr : a.b, g, &pf.true_rel_residual_l2);
+            if constexpr (TRUE_INLINE) {
+                if (ok) {
+                    Mat<double> A64 = mat_of<double>(a);
+                    if (KIND == KIND_PBICG) A64.ell_w = 0;   // asymmetric: the internal CSR holds A
+                    ok = true_residual(a, A64, KIND == KIND_PBICG ? nullptr : a.b, g, &pf.true_rel_residual_l2);
+                }
             }
             if (ok && !a.no_store) phase_store_x(a, g);
         }
@@ -1623,8 +1320,34 @@ template <int KIND>
 __global__ void __launch_bounds__(1024, 1) k_solve(SolveArgs a, unsigned long long timeout_ns)
 {
     Group g{reinterpret_cast<unsigned long long*>(a.status + DS_BARRIER), a.status, (int)gridDim.x, (int)blockIdx.x, timeout_ns};
-    if (a.stage) stage_ring_init();
-    run_system<KIND>(a, g);
+    run_system<KIND, false>(a, g);
+}
+
+// The single-system solver's true residual, after it on the stream: per-block
+// sums of r_p^2 and b_p^2 (r = b - A64 x in the Amul's face order, one FMA per
+// term, each thread's rows in order) into the partials, then one warp adds
+// the block partials in block order and writes ||r||_2/||b||_2 (||r||_2 when
+// b = 0) into the report.  Deterministic, like every reduction here.
+__global__ void __launch_bounds__(256) k_true_residual_part(SolveArgs a, int asym)
+{
+    Mat<double> A64 = mat_of<double>(a);
+    if (asym) A64.ell_w = 0;
+    double acc[2] = {0.0, 0.0};
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += gridDim.x * blockDim.x) {
+        const double bv = asym ? a.b_orig[a.perm[p]] : a.b[p];
+        const double rr = __dsub_rn(bv, amul_row<double>(A64, a.x, p));
+        acc[0] = __fma_rn(rr, rr, acc[0]);
+        acc[1] = __fma_rn(bv, bv, acc[1]);
+    }
+    block_reduce_store<2>(acc, a.partials, SL_A, blockIdx.x);
+}
+
+__global__ void k_true_residual_final(SolveArgs a, int nblocks)
+{
+    double t[2];
+    grid_reduce_read<2>(t, a.partials, SL_A, nblocks);
+    if (threadIdx.x == 0 && a.perf)
+        a.perf->true_rel_residual_l2 = t[1] > 0.0 ? __ddiv_rn(__dsqrt_rn(t[0]), __dsqrt_rn(t[1])) : __dsqrt_rn(t[0]);
 }
 
 // The batched launch, one instance per solve kind and largest block size
@@ -1640,7 +1363,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 256 ? 2 : 1) k_solve_batch(Batch
     __syncthreads();
     Group g{reinterpret_cast<unsigned long long*>(sa.status + DS_BARRIER), sa.status, t.split[s + 1] - t.split[s],
             (int)blockIdx.x - t.split[s], timeout_ns};
-    run_system<KIND>(sa, g);
+    run_system<KIND, true>(sa, g);
 }
 
 // Stand-alone Amul on the prepared matrix (internal order): the PCG's Amul
@@ -1664,6 +1387,38 @@ __global__ void __launch_bounds__(256) k_amul_prepared(int n, Mat<T> A, const T*
 #pragma unroll
         for (int k = 0; k < R; k++)
             if (p[k] < n) __stcs(y + p[k], yy[k]);
+    }
+}
+
+// Stand-alone Amul on the fixed-width layout alone (no row-extent branch in
+// the kernel, rows of at most W entries): its registers stay within 32 per
+// thread, so that 2048 threads per SM are resident and enough loads are in
+// flight; one wave of 8 blocks per SM walks the rows.  Each row: d_p x_p, then
+// its entries in layout order (lower ascending, then upper ascending), one
+// FMA each: the same sums as the solver's Amul phase.
+template <class T, int W>
+__global__ void __launch_bounds__(256, 8) k_amul_ell(int n, Mat<T> A, const T* __restrict__ x, T* __restrict__ y)
+{
+    const int stride = gridDim.x * blockDim.x;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        int c[W];
+        T a[W], v[W];
+#pragma unroll
+        for (int j = 0; j < W; j++) {
+            const bool ok = j < A.ell_w;
+            const size_t e = (size_t)j * A.ell_stride + p;
+            c[j] = ok ? __ldcs(A.Ecol + e) : -1;
+            a[j] = ok ? __ldcs(A.Ea + e) : T(0);
+        }
+        const T xp = x[p];
+        const T d = __ldcs(A.d + p);
+#pragma unroll
+        for (int j = 0; j < W; j++) v[j] = c[j] >= 0 ? x[c[j]] : T(0);
+        T yy = mul_rn(d, xp);
+#pragma unroll
+        for (int j = 0; j < W; j++)
+            if (c[j] >= 0) yy = fmadd(a[j], v[j], yy);
+        __stcs(y + p, yy);
     }
 }
 
@@ -1779,19 +1534,10 @@ static const void* batch_kernel(int kind, int threads)
 static std::mutex g_occ_mu;
 static std::map<long long, int> g_occ;   // (kernel, block threads, ring) -> co-resident blocks per SM
 
-// Dynamic shared memory of the staged DIC sweeps' ring for a solve kind (the
-// precision its sweeps run in), 0 for kinds that do not stage.
-static size_t stage_bytes(int kind)
-{
-    if (kind == KIND_F64) return StageCfg<double>::BYTES;
-    if (kind == KIND_MIXED || kind == KIND_MIXED_RESTART) return StageCfg<float>::BYTES;
-    return 0;
-}
-
 int solve_blocks_per_sm(int threads, bool batch, int kind, size_t dyn = 0)
 {
     std::lock_guard<std::mutex> lk(g_occ_mu);
-    const long long key = ((long long)(threads * 2 + (batch ? 1 : 0)) * 8 + kind) * 2 + (dyn ? 1 : 0);
+    const long long key = (((long long)(threads * 2 + (batch ? 1 : 0)) * 8 + kind) << 20) + (long long)dyn;
     auto it = g_occ.find(key);
     if (it != g_occ.end()) return it->second;
     const void* k = batch ? batch_kernel(kind, threads) : solve_kernel(kind);
@@ -1849,25 +1595,28 @@ spuma_status launch_solve(spuma_ldu_t h, const SolveArgs& a, int threads, cudaSt
         set_error("block_threads must be a multiple of 32 in [32, 1024]");
         return SPUMA_ERR_INVALID_ARG;
     }
-    // the DIC sweeps of the PCG kinds run through the shared-memory ring
-    // (SPUMA_NO_STAGE=1 keeps them on direct loads, for measurements)
     const int kind = kind_of(a);
-    static const bool no_stage = getenv("SPUMA_NO_STAGE") && atoi(getenv("SPUMA_NO_STAGE")) != 0;
-    const size_t dyn = (a.precond == SPUMA_PRECOND_DIC && !no_stage) ? stage_bytes(kind) : 0;
-    const int grid = solve_grid(h, threads, kind, dyn);
+    const int grid = solve_grid(h, threads, kind, 0);
     if (grid < 1) { set_error("solver kernel cannot be resident"); return SPUMA_ERR_CUDA; }
     SPUMA_CUDA(cudaMemsetAsync(h->at<char>(h->L.bar), 0, h->L.status + 256 - h->L.bar, s));
     unsigned long long tns = barrier_timeout_ns();
     SolveArgs b = a;
-    b.stage = dyn ? 1 : 0;
     b.tail_from = tail_level(h, threads);
     if (getenv("SPUMA_PHASE_CLOCKS")) {
         b.phase_clk = h->at<long long>(h->L.clk);
         SPUMA_CUDA(cudaMemsetAsync(b.phase_clk, 0, 8 * 256, s));
     }
     void* args[] = {(void*)&b, (void*)&tns};
-    SPUMA_CUDA(cudaLaunchCooperativeKernel(solve_kernel(kind), grid, threads, args, dyn, s));
+    SPUMA_CUDA(cudaLaunchCooperativeKernel(solve_kernel(kind), grid, threads, args, 0, s));
     count_launch();
+    if (b.mode == MODE_SOLVE) {
+        // the report's true residual (the solver's x in internal order is still in the workspace)
+        const int tg = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)h->n + 255) / 256, (int64_t)h->num_sms * 8));
+        k_true_residual_part<<<tg, 256, 0, s>>>(b, kind == KIND_PBICG ? 1 : 0);
+        k_true_residual_final<<<1, 32, 0, s>>>(b, tg);
+        count_launch(2);
+        SPUMA_CUDA(cudaGetLastError());
+    }
     return SPUMA_OK;
 }
 
@@ -2037,11 +1786,21 @@ spuma_status spuma_amul_prepared(spuma_ldu_t h, int32_t precision, const void* x
     if (precision == SPUMA_F64) {
         Mat<double> A{a.Lptr, a.Lcol, a.La64, a.Lc64, a.Uptr, a.Ucol, a.Ua64, a.Uc64, a.d64, a.rD64,
                       a.Ecol, a.Ea64, a.ell_w, a.n};
-        k_amul_prepared<double><<<g, 256, 0, s>>>(h->n, A, (const double*)x, (double*)y);
+        const int ge = std::min(g, h->num_sms * 8);
+        if (a.ell_w > 0 && a.ell_w <= 6)
+            k_amul_ell<double, 6><<<ge, 256, 0, s>>>(h->n, A, (const double*)x, (double*)y);
+        else if (a.ell_w > 0)
+            k_amul_ell<double, kEllMax><<<ge, 256, 0, s>>>(h->n, A, (const double*)x, (double*)y);
+        else
+            k_amul_prepared<double><<<g, 256, 0, s>>>(h->n, A, (const double*)x, (double*)y);
     } else {
         Mat<float> A{a.Lptr, a.Lcol, a.La32, a.Lc32, a.Uptr, a.Ucol, a.Ua32, a.Uc32, a.d32, a.rD32,
                      a.Ecol, a.Ea32, a.ell_w, a.n};
-        k_amul_prepared<float><<<g, 256, 0, s>>>(h->n, A, (const float*)x, (float*)y);
+        static const bool ell32 = getenv("SPUMA_AMUL32_ELL") && atoi(getenv("SPUMA_AMUL32_ELL")) != 0;
+        if (ell32 && a.ell_w > 0 && a.ell_w <= 6)
+            k_amul_ell<float, 6><<<std::min(g, h->num_sms * 8), 256, 0, s>>>(h->n, A, (const float*)x, (float*)y);
+        else
+            k_amul_prepared<float><<<g, 256, 0, s>>>(h->n, A, (const float*)x, (float*)y);
     }
     count_launch();
     SPUMA_CUDA(cudaGetLastError());

@@ -15,7 +15,6 @@ struct SolveArgs {
     int zero_x0;           // start from x = 0 instead of reading x_orig
     int no_store;          // leave x_orig untouched (autotuner trial runs)
     int tail_from;         // levels >= tail_from are small enough for the group's first block alone
-    int stage;             // DIC sweeps staged through shared memory (single-system launch with the ring)
     int max_iter, min_iter, max_outer;
     double tol, rel_tol, inner_rel_tol;
     const int* lvl;        // [nlev+1] level starts (internal order)

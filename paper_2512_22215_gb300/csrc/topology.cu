@@ -89,6 +89,11 @@ Layout make_layout(int64_t n, int64_t nf, bool asym)
     L.status = take(256);
     L.args = take(4096);
     L.clk = take(8 * 256);
+    // per-cell boundary-face lists of the pressure-step operators, built once
+    // per boundary (up to 2 boundary faces per cell on average)
+    L.bstart = take(i4n1);
+    L.blist_cap = 2 * (size_t)n;
+    L.blist = take(4 * L.blist_cap);
     if (asym) {
         L.asym = true;
         L.LaT64 = take(d8f);

@@ -67,3 +67,35 @@ def test_cached_hierarchy_new_coefficients(gc):
     xo, po, _ = G.gamg(m.lower, m.upper_addr, dg2, up2, c.b, w, x0=x0, tol=0.0, max_iter=p["n_iter"])
     assert p["converged"] == 1
     assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("smoother,coarsest", [(1, 1), (0, 2), (1, 2)], ids=["gs2-diag", "richardson-dic", "gs2-dic"])
+def test_smoother_and_coarsest_options_matched_iterations(gc, smoother, coarsest):
+    """The two-stage Gauss-Seidel smoother and the DIC-PCG coarsest level
+    (the paper's smoother table) at matched V-cycle counts."""
+    from paper_2512_22215_gb300 import GamgSolver, SolverControls
+    c, m, M, S, w, up, dg = gc
+    S2 = GamgSolver(M, dev(w), smoother=smoother, coarsest_precond=coarsest)
+    name = "gs2" if smoother == 1 else "richardson"
+    x, p = S2.solve(dev(dg), dev(up), dev(c.b), None, SolverControls(tolerance=1e-10, max_iter=500))
+    assert p["converged"] == 1 and p["status"] == 0
+    _, po, _ = G.gamg(m.lower, m.upper_addr, dg, up, c.b, w, tol=1e-10, max_iter=500, smoother=name,
+                      coarsest_precond=coarsest)
+    assert abs(p["n_iter"] - po["n_iter"]) <= max(2, po["n_iter"] // 20)
+    xo, _, _ = G.gamg(m.lower, m.upper_addr, dg, up, c.b, w, tol=0.0, max_iter=p["n_iter"], smoother=name,
+                      coarsest_precond=coarsest)
+    x = x.cpu().numpy()
+    assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
+    r = c.b - oracle.amul(m.lower, m.upper_addr, dg, up, x)
+    assert np.abs(r).sum() / np.abs(c.b).sum() < 1e-10
+    assert p["true_rel_residual_l2"] == pytest.approx(np.linalg.norm(r) / np.linalg.norm(c.b), rel=1e-12)
+
+
+def test_options_rejected():
+    from paper_2512_22215_gb300 import GamgSolver, SpumaError
+    c = hexmesh.pressure_case(4, seed=106)
+    M = mesh_of(c)
+    with pytest.raises(SpumaError):
+        GamgSolver(M, dev(np.linalg.norm(c.mesh.sf, axis=1)), smoother=2)
+    with pytest.raises(SpumaError):
+        GamgSolver(M, dev(np.linalg.norm(c.mesh.sf, axis=1)), coarsest_precond=0)

@@ -133,13 +133,13 @@ def test_batch_64_systems_log_uniform():
     log-uniform in 1e4..5e5 (sides from hexmesh.batch_sizes, seed 5; 8.2M
     cells), FP64 and mixed, tuned and replayed from a CUDA graph.  Every system
     reaches the oracle's FP64 residual 1e-8; FP64 systems of at most 64^3
-    cells match the oracle's PCG at the same iteration count: to 1e-10 up to
-    130 iterations, to 1e-8 beyond.  The looser bound is the arithmetic's, not
-    the kernel's: two FP64 PCG runs that differ only in the order of their
-    dot-product sums (the oracle's sequential sums against pairwise ones, both
-    on the CPU with the oracle's Amul and DIC) drift apart by 8.6e-14 at 22^3
-    (91 iterations), 3.6e-11 at 32^3 (129), 1.4e-9 at 44^3 (181) and 7.9e-10
-    at 62^3 (248); the GPU's fixed reduction tree is such an order."""
+    cells match the oracle's PCG at the same iteration count to 1e-8.  That
+    bound is the arithmetic's, not the kernel's: two FP64 PCG runs on the CPU
+    that differ only in the order of their dot-product sums (the oracle's
+    sequential sums against pairwise ones, with the oracle's Amul and DIC)
+    drift apart by 8.9e-10 on this batch's 23^3 system (seed 504, 96
+    iterations) and 8.1e-10 at 62^3 (seed 500, 248 iterations); the GPU's
+    fixed reduction tree is such an order."""
     from paper_2512_22215_gb300 import MIXED, BatchSolve, LduMesh, SolverControls
     sides = hexmesh.batch_sizes(64, seed=5)
     cs = [hexmesh.pressure_case(n, jitter=0.2, permute=True, seed=500 + k, lognormal_gamma=True)
@@ -165,8 +165,7 @@ def test_batch_64_systems_log_uniform():
             if precision == 0 and m.n_cells <= 64 ** 3:
                 xo, _ = oracle.pcg(m.lower, m.upper_addr, dgs[k], ups[k], c.b, precond=2, tol=0.0,
                                    max_iter=res[k]["n_iter"])
-                bound = 1e-10 if res[k]["n_iter"] <= 130 else 1e-8
-                assert np.linalg.norm(x - xo) <= bound * np.linalg.norm(xo), (k, res[k]["n_iter"])
+                assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo), (k, res[k]["n_iter"])
 
 
 def test_autograd_dense_gradient_8cubed():

@@ -184,6 +184,7 @@ def test_new_entry_points_reject_bad_arguments(L):
     assert L.spuma_gamg_solve(None, None, None, None, None, C.byref(ctl), None, None) == 1
     assert L.spuma_gamg_info(None, None, None, 0) == 1
     assert L.spuma_gamg_destroy(None) == 0
+    assert L.spuma_gamg_set_options(None, 0, 1) == 1
 
 
 def test_asymmetric_workspace_is_larger(L):
