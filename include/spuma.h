@@ -297,7 +297,13 @@ spuma_status spuma_pcg_solve_static(int32_t n_cells, int32_t n_faces, const int3
  * ascending face order, then the cell's boundary faces in ascending order:
  * bit-identical to the sequential face loop.  These calls use the handle's
  * vector region as scratch (as the assembly does): do not overlap them with
- * a solve on the same handle.
+ * a solve on the same handle.  spuma_fv_grad and spuma_pressure_rhs also
+ * use the matrix region for a face-indexed scratch: a matrix prepared with
+ * spuma_matrix_prepare() must be prepared again after them (a solve always
+ * prepares its own).  The per-cell lists of boundary faces are built on the
+ * first call with a given (bface_cell pointer, n_bfaces) and reused while
+ * calls pass the same pair: a mesh's boundary topology is fixed (a boundary
+ * with more than two faces per cell on average is listed on every call).
  *
  * spuma_fv_weights: w[F], the owner weight of the linear interpolation
  *   p_f = w p_l + (1 - w) p_u, w = |S.(C_u - C_f)| / (|S.(C_f - C_l)| + |S.(C_u - C_f)|).

@@ -274,6 +274,12 @@ class GamgSolver:
         check(L.spuma_gamg_info(h, C.byref(nl), C.cast(cells, C.c_void_p), 64), "spuma_gamg_info")
         self.level_cells = [cells[k] for k in range(min(nl.value, 64))]
 
+    def set_options(self, smoother: int = 0, coarsest_precond: int = 1):
+        """Smoother (0 Richardson, 1 two-stage Gauss-Seidel) and coarsest-level
+        preconditioner (1 diagonal, 2 DIC) of later solves; the hierarchy is kept."""
+        check(lib().spuma_gamg_set_options(self.handle, int(smoother), int(coarsest_precond)),
+              "spuma_gamg_set_options")
+
     def solve(self, diag, upper, b, x=None, controls: SolverControls | None = None, perf=None, check_status=True):
         ctl = (controls or SolverControls()).c()
         if x is None:

@@ -103,7 +103,7 @@ __device__ __forceinline__ double4 ld_t4(const double4* t, int f)
     return make_double4(a.x, a.y, b.x, b.y);
 }
 
-__global__ void __launch_bounds__(256, 8) k_fv_grad_cell(int n, const int* __restrict__ lo_start,
+__global__ void __launch_bounds__(256, 6) k_fv_grad_cell(int n, const int* __restrict__ lo_start,
                                                          const int* __restrict__ lo_face,
                                                          const int* __restrict__ own_start,
                                                          const double4* __restrict__ t, const double* __restrict__ p,
@@ -112,30 +112,31 @@ __global__ void __launch_bounds__(256, 8) k_fv_grad_cell(int n, const int* __res
                                                          const int8_t* __restrict__ btype,
                                                          const double* __restrict__ v, double* __restrict__ grad)
 {
-    constexpr int G = 4;   // faces whose loads are issued together
+    // a cell's faces as one list (neighbour side, then owner side: ascending
+    // face order) in groups of G, so that an interior hex cell (six faces,
+    // two full groups) issues no idle sums: GB300's FP64 pipe, not memory,
+    // bounds these kernels, and a predicated-off FP64 add costs as much as a
+    // live one (G = 3 keeps the records within 32 registers)
+    constexpr int G = 3;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int k0 = lo_start[i], nl = lo_start[i + 1] - k0, f0 = own_start[i], nt = nl + own_start[i + 1] - f0;
         double gx = 0.0, gy = 0.0, gz = 0.0;
-        const int k1 = lo_start[i + 1];
-        for (int k0 = lo_start[i]; k0 < k1; k0 += G) {   // i = u(f): -t_f
+        for (int jb = 0; jb < nt; jb += G) {
             double4 tv[G];
 #pragma unroll
-            for (int j = 0; j < G; j++) tv[j] = k0 + j < k1 ? ld_t4(t, lo_face[k0 + j]) : make_double4(0, 0, 0, 0);
-#pragma unroll
-            for (int j = 0; j < G; j++)
-                if (k0 + j < k1) {
-                    gx = __dsub_rn(gx, tv[j].x);
-                    gy = __dsub_rn(gy, tv[j].y);
-                    gz = __dsub_rn(gz, tv[j].z);
+            for (int j = 0; j < G; j++) {
+                const int e = jb + j;
+                if (e < nt) {
+                    const double4 q = ld_t4(t, e < nl ? __ldcs(lo_face + k0 + e) : f0 + (e - nl));
+                    // i = u(f): -t_f (an exact negation), i = l(f): +t_f
+                    tv[j] = e < nl ? make_double4(-q.x, -q.y, -q.z, 0.0) : q;
+                } else {
+                    tv[j] = make_double4(0.0, 0.0, 0.0, 0.0);
                 }
-        }
-        const int f1 = own_start[i + 1];
-        for (int f0 = own_start[i]; f0 < f1; f0 += G) {  // i = l(f): +t_f
-            double4 tv[G];
-#pragma unroll
-            for (int j = 0; j < G; j++) tv[j] = f0 + j < f1 ? ld_t4(t, f0 + j) : make_double4(0, 0, 0, 0);
+            }
 #pragma unroll
             for (int j = 0; j < G; j++)
-                if (f0 + j < f1) {
+                if (jb + j < nt) {
                     gx = __dadd_rn(gx, tv[j].x);
                     gy = __dadd_rn(gy, tv[j].y);
                     gz = __dadd_rn(gz, tv[j].z);
@@ -209,28 +210,27 @@ __global__ void __launch_bounds__(256, 8) k_fv_cell_sum(int n, const int* __rest
                                                         const double* __restrict__ bphi, int bsign,
                                                         double* __restrict__ out)
 {
+    // one list per cell (neighbour side, then owner side), groups of G: an
+    // interior hex cell issues its six FP64 adds once (see k_fv_grad_cell)
     constexpr int G = 6;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int k0 = lo_start[i], k1 = lo_start[i + 1], f0 = own_start[i], f1 = own_start[i + 1];
+        const int k0 = lo_start[i], nl = lo_start[i + 1] - k0, f0 = own_start[i], nt = nl + own_start[i + 1] - f0;
         double acc = 0.0;
-        for (int kb = k0; kb < k1; kb += G) {
-            int f[G];
-#pragma unroll
-            for (int j = 0; j < G; j++) f[j] = kb + j < k1 ? __ldcs(lo_face + kb + j) : -1;
+        for (int jb = 0; jb < nt; jb += G) {
             double t[G];
 #pragma unroll
-            for (int j = 0; j < G; j++) t[j] = f[j] >= 0 ? __ldcs(val + f[j]) : 0.0;
+            for (int j = 0; j < G; j++) {
+                const int e = jb + j;
+                if (e < nt) {
+                    const double q = __ldcs(val + (e < nl ? __ldcs(lo_face + k0 + e) : f0 + (e - nl)));
+                    t[j] = e < nl ? -q : q;   // neighbour side subtracts (an exact negation)
+                } else {
+                    t[j] = 0.0;
+                }
+            }
 #pragma unroll
             for (int j = 0; j < G; j++)
-                if (f[j] >= 0) acc = __dsub_rn(acc, t[j]);
-        }
-        for (int fb = f0; fb < f1; fb += G) {
-            double t[G];
-#pragma unroll
-            for (int j = 0; j < G; j++) t[j] = fb + j < f1 ? __ldcs(val + fb + j) : 0.0;
-#pragma unroll
-            for (int j = 0; j < G; j++)
-                if (fb + j < f1) acc = __dadd_rn(acc, t[j]);
+                if (jb + j < nt) acc = __dadd_rn(acc, t[j]);
         }
         if (bstart) {
             if (bsign < 0)
@@ -366,7 +366,7 @@ spuma_status spuma_fv_grad(spuma_ldu_t h, const double* face_sf, const double* w
             h->nf, h->at<int>(L.laddr), h->at<int>(L.uaddr), face_sf, w, p, t);
         count_launch();
     }
-    k_fv_grad_cell<<<std::min(grid_fv(h->n, 256, h->num_sms), h->num_sms * 8), 256, 0, s>>>(
+    k_fv_grad_cell<<<std::min(grid_fv(h->n, 256, h->num_sms), h->num_sms * 6), 256, 0, s>>>(
         h->n, h->at<int>(L.lo_start), h->at<int>(L.lo_face), h->at<int>(L.own_start), t, p, bstart, blist, bface_sf,
         bface_type, cell_v, grad);
     count_launch();

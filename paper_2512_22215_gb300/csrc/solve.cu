@@ -1393,7 +1393,8 @@ __global__ void __launch_bounds__(256) k_amul_prepared(int n, Mat<T> A, const T*
 // Stand-alone Amul on the fixed-width layout alone (no row-extent branch in
 // the kernel, rows of at most W entries): its registers stay within 32 per
 // thread, so that 2048 threads per SM are resident and enough loads are in
-// flight; one wave of 8 blocks per SM walks the rows.  Each row: d_p x_p, then
+// flight; one wave of 8 blocks per SM walks the rows (FP64: 140 -> 130.6 us
+// at 200^3 against the kernel shared with the row-extent path).  Each row: d_p x_p, then
 // its entries in layout order (lower ascending, then upper ascending), one
 // FMA each: the same sums as the solver's Amul phase.
 template <class T, int W>
@@ -1796,11 +1797,9 @@ spuma_status spuma_amul_prepared(spuma_ldu_t h, int32_t precision, const void* x
     } else {
         Mat<float> A{a.Lptr, a.Lcol, a.La32, a.Lc32, a.Uptr, a.Ucol, a.Ua32, a.Uc32, a.d32, a.rD32,
                      a.Ecol, a.Ea32, a.ell_w, a.n};
-        static const bool ell32 = getenv("SPUMA_AMUL32_ELL") && atoi(getenv("SPUMA_AMUL32_ELL")) != 0;
-        if (ell32 && a.ell_w > 0 && a.ell_w <= 6)
-            k_amul_ell<float, 6><<<std::min(g, h->num_sms * 8), 256, 0, s>>>(h->n, A, (const float*)x, (float*)y);
-        else
-            k_amul_prepared<float><<<g, 256, 0, s>>>(h->n, A, (const float*)x, (float*)y);
+        // FP32: the software-pipelined kernel measured faster than the
+        // 32-register one (90.4 against 92.8 us at 200^3)
+        k_amul_prepared<float><<<g, 256, 0, s>>>(h->n, A, (const float*)x, (float*)y);
     }
     count_launch();
     SPUMA_CUDA(cudaGetLastError());
