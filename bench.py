@@ -33,7 +33,8 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # bench workload by the per-iteration byte model (traffic grows with the
 # algorithmic bytes).  Valid only for the solver source it was taken with
 # (checked by hash, else the line reports null).
-TRAFFIC = {"solve_cu_sha1": None, "n": 128, "bytes": None, "inner": None, "outer": None}
+TRAFFIC = {"solve_cu_sha1": "e38f005bfad22fbacd8fce247ec9fc932dcf3331", "n": 128,
+           "bytes": 124835436544 + 2192241664, "inner": 524, "outer": 4}
 # Iteration counts of this seeded workload (mixed: inner iterations, outer
 # steps), used only to project the CPU oracle's bounded sample to a full solve.
 PROJECTION_ITERS = {"inner": 795, "outer": 5}
@@ -50,6 +51,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", action="store_true",
                     help="time the batched workload instead: 64 systems, cells log-uniform in 1e4..5e5")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="one launch of each hot kernel on the n^3 workload (for profiler captures): no timing")
+    ap.add_argument("--seed", type=int, default=None, help="workload seed (default 3 at 200^3, else 2)")
     return ap.parse_args()
 
 
@@ -185,9 +189,51 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_case(n: int):
+def make_case(n: int, seed=None):
     import hexmesh
-    return hexmesh.pressure_case(n, jitter=0.2, permute=True, seed=3, lognormal_gamma=True)
+    if seed is None:
+        seed = 3 if n == 200 else 2
+    return hexmesh.pressure_case(n, jitter=0.2, permute=True, seed=seed, lognormal_gamma=True)
+
+
+def profile_run(args, local):
+    """One launch of each hot kernel on the n^3 workload, in this order: the
+    assembly, a mixed solve, an FP64 solve, the pressure-step operators
+    (weights, gradient, right-hand side, flux, divergence) and the stand-alone
+    FP64 and FP32 Amul on the prepared matrix.  For profiler captures (-k
+    selects the kernel); prints one line."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2512_22215_gb300 import MIXED, LduMesh, SolverControls
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case = make_case(args.n, args.seed)
+    m = case.mesh
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    M = LduMesh(m.lower, m.upper_addr, m.n_cells, device=dev, centres=m.c)
+    sf, cc, cf, v = T(m.sf), T(m.c), T(m.cf), T(m.v)
+    bcell, bsf, bcf, bg, bt = T(m.bface_cell), T(m.bface_sf), T(m.bface_cf), T(case.bgamma), T(case.btype)
+    gamma, b = T(case.gamma), T(case.b)
+    up, dg = M.assemble_laplacian(sf, cc, gamma, bcell, bsf, bcf, bg, bt)
+    _, pm = M.solve(dg, up, b, None, SolverControls(precond=2, precision=MIXED, tolerance=1e-8))
+    _, pf = M.solve(dg, up, b, None, SolverControls(precond=2, tolerance=1e-8))
+    rng = np.random.default_rng(7)
+    phi = T(rng.standard_normal(m.n_faces) * np.linalg.norm(m.sf, axis=1))
+    bphi = T(rng.standard_normal(m.n_bfaces) * np.linalg.norm(m.bface_sf, axis=1))
+    w = M.fv_weights(sf, cf, cc)
+    g = M.fv_grad(sf, w, v, b, bcell, bsf, bt)
+    corr, _ = M.pressure_rhs(sf, cc, w, gamma, g, phi, bcell, bphi)
+    M.pressure_flux(up, corr, b, phi, cc, bcell, bsf, bcf, bg, bt, bphi)
+    M.fv_div(phi, bcell, bphi)
+    M.prepare(dg, up, 2)
+    xi = M.to_internal(b)
+    M.amul_prepared(xi)
+    M.amul_prepared(xi.float())
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": f"{args.n}^3", "cells": m.n_cells, "faces": m.n_faces,
+                      "mixed_iters": pm["n_iter"], "fp64_iters": pf["n_iter"]}), flush=True)
 
 
 def cpu_sample(case, n_inner_sample: int):
@@ -225,7 +271,7 @@ def run_reference(args, rank, world):
     """The oracle as the reference arm (rank 0 only)."""
     if rank != 0:
         return
-    case = make_case(args.n)
+    case = make_case(args.n, args.seed)
     cores = 1
     vals = []
     info = {}
@@ -368,6 +414,10 @@ def main():
     if args.batch:
         run_batch(args, rank, world, local)
         return
+    if args.profile_run:
+        if rank == 0:
+            profile_run(args, local)
+        return
     import numpy as np
     import torch
     if world > 1:
@@ -381,7 +431,7 @@ def main():
     from paper_2512_22215_gb300 import MIXED, LduMesh, SolverControls, lib
     from paper_2512_22215_gb300.core import perf_tensor, read_perf
 
-    case = make_case(args.n)
+    case = make_case(args.n, args.seed)
     m = case.mesh
     N, F = m.n_cells, m.n_faces
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)

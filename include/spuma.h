@@ -265,7 +265,7 @@ spuma_status spuma_pcg_solve(spuma_ldu_t h, const double* diag, const double* up
  * code path that must not pay cudaMalloc's implicit synchronisation).  The
  * mesh topology and all solver scratch live in one static device array of
  * spuma_static_workspace_bytes() bytes (32 MiB, enough for hex meshes of
- * about 70 thousand cells) that every GPU loading the library holds until the
+ * about 65 thousand cells) that every GPU loading the library holds until the
  * process exits; a larger mesh is rejected with SPUMA_ERR_WORKSPACE_TOO_SMALL
  * before any device work.  The caller passes the addressing, the
  * coefficients, b, x (initial guess in, solution out) and perf, all device

@@ -274,6 +274,8 @@ struct Layout {
     size_t La32, Ua32, Lc32, Uc32, d32, rD32;
     // fixed-width Amul layout: ell_slots entries
     size_t ell_slots, Ecol, Ea64, Ea32;
+    // the cells' faces, fixed-width column-major in original cell order (same width)
+    size_t FL;
     // vectors
     size_t x64, r64, w64, p64, q64, b64;
     size_t x32, r32, w32, p32, q32;

@@ -159,6 +159,99 @@ __global__ void __launch_bounds__(256, 6) k_fv_grad_cell(int n, const int* __res
     }
 }
 
+// The same two cell passes over the fixed-width face lists (entry j of cell
+// i at FL[j n + i]: -(f + 1) neighbour side, f + 1 owner side, 0 padding; the
+// neighbour-side faces first, each side ascending: the face order): a
+// thread's face indices arrive in W coalesced loads with no extents to load
+// first, then its values in one gather round.
+__device__ __forceinline__ int fl_face(int v) { return v > 0 ? v - 1 : -v - 1; }
+
+template <int W>
+__global__ void __launch_bounds__(256, 6) k_fv_grad_cell_fl(int n, const int* __restrict__ FL,
+                                                            const double4* __restrict__ t,
+                                                            const double* __restrict__ p,
+                                                            const int* __restrict__ bstart,
+                                                            const int* __restrict__ blist,
+                                                            const double* __restrict__ bsf,
+                                                            const int8_t* __restrict__ btype,
+                                                            const double* __restrict__ v, double* __restrict__ grad)
+{
+    constexpr int H = (W + 1) / 2;   // records gathered in two rounds of H (registers)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int e[W];
+#pragma unroll
+        for (int j = 0; j < W; j++) e[j] = __ldcs(FL + (size_t)j * n + i);
+        double gx = 0.0, gy = 0.0, gz = 0.0;
+#pragma unroll
+        for (int h = 0; h < W; h += H) {
+            double4 tv[H];
+#pragma unroll
+            for (int j = 0; j < H; j++) {
+                const int ej = h + j < W ? e[h + j] : 0;
+                if (ej != 0) {
+                    const double4 q = ld_t4(t, fl_face(ej));
+                    tv[j] = ej < 0 ? make_double4(-q.x, -q.y, -q.z, 0.0) : q;   // exact negation
+                } else {
+                    tv[j] = make_double4(0.0, 0.0, 0.0, 0.0);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < H; j++)
+                if (h + j < W && e[h + j] != 0) {
+                    gx = __dadd_rn(gx, tv[j].x);
+                    gy = __dadd_rn(gy, tv[j].y);
+                    gz = __dadd_rn(gz, tv[j].z);
+                }
+        }
+        if (bstart) {
+            const double pi = p[i];
+            for (int k = bstart[i]; k < bstart[i + 1]; k++) {
+                const int b = blist[k];
+                const double pb = btype[b] == 1 ? 0.0 : pi;
+                gx = __dadd_rn(gx, __dmul_rn(bsf[3 * (size_t)b + 0], pb));
+                gy = __dadd_rn(gy, __dmul_rn(bsf[3 * (size_t)b + 1], pb));
+                gz = __dadd_rn(gz, __dmul_rn(bsf[3 * (size_t)b + 2], pb));
+            }
+        }
+        const double vi = v[i];
+        grad[3 * (size_t)i + 0] = __ddiv_rn(gx, vi);
+        grad[3 * (size_t)i + 1] = __ddiv_rn(gy, vi);
+        grad[3 * (size_t)i + 2] = __ddiv_rn(gz, vi);
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(256, 8) k_fv_cell_sum_fl(int n, const int* __restrict__ FL,
+                                                           const double* __restrict__ val,
+                                                           const int* __restrict__ bstart,
+                                                           const int* __restrict__ blist,
+                                                           const double* __restrict__ bphi, int bsign,
+                                                           double* __restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int e[W];
+#pragma unroll
+        for (int j = 0; j < W; j++) e[j] = __ldcs(FL + (size_t)j * n + i);
+        double t[W];
+#pragma unroll
+        for (int j = 0; j < W; j++) {
+            const double q = e[j] != 0 ? __ldcs(val + fl_face(e[j])) : 0.0;
+            t[j] = e[j] < 0 ? -q : q;   // neighbour side subtracts (an exact negation)
+        }
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < W; j++)
+            if (e[j] != 0) acc = __dadd_rn(acc, t[j]);
+        if (bstart) {
+            if (bsign < 0)
+                for (int k = bstart[i]; k < bstart[i + 1]; k++) acc = __dsub_rn(acc, bphi[blist[k]]);
+            else
+                for (int k = bstart[i]; k < bstart[i + 1]; k++) acc = __dadd_rn(acc, bphi[blist[k]]);
+        }
+        __stcs(out + i, acc);
+    }
+}
+
 // Explicit non-orthogonal correction flux of the corrected laplacian:
 // corr_f = (gamma_f |S|) (k . (w grad_l + (1 - w) grad_u)), k = S/|S| - d delta,
 // delta = 1/max(n.d, 0.05 |d|) (the implicit part's coefficient).
@@ -240,6 +333,20 @@ __global__ void __launch_bounds__(256, 8) k_fv_cell_sum(int n, const int* __rest
         }
         __stcs(out + i, acc);
     }
+}
+
+// Cell sums of one face array over whichever face lists the handle has.
+static void launch_cell_sum(spuma_ldu_t h, const double* val, const int* bstart, const int* blist,
+                            const double* bphi, int bsign, double* out, cudaStream_t s)
+{
+    const Layout& L = h->L;
+    const int g = std::min(grid_fv(h->n, 256, h->num_sms), h->num_sms * 8);
+    if (h->ell_w > 0 && h->ell_w <= 6)
+        k_fv_cell_sum_fl<6><<<g, 256, 0, s>>>(h->n, h->at<int>(L.FL), val, bstart, blist, bphi, bsign, out);
+    else
+        k_fv_cell_sum<<<g, 256, 0, s>>>(h->n, h->at<int>(L.lo_start), h->at<int>(L.lo_face), h->at<int>(L.own_start),
+                                        val, bstart, blist, bphi, bsign, out);
+    count_launch();
 }
 
 // phi_f = phiHbyA_f - (a_f (p_u - p_l) + corr_f), a_f = -upper_f.
@@ -366,9 +473,14 @@ spuma_status spuma_fv_grad(spuma_ldu_t h, const double* face_sf, const double* w
             h->nf, h->at<int>(L.laddr), h->at<int>(L.uaddr), face_sf, w, p, t);
         count_launch();
     }
-    k_fv_grad_cell<<<std::min(grid_fv(h->n, 256, h->num_sms), h->num_sms * 6), 256, 0, s>>>(
-        h->n, h->at<int>(L.lo_start), h->at<int>(L.lo_face), h->at<int>(L.own_start), t, p, bstart, blist, bface_sf,
-        bface_type, cell_v, grad);
+    const int gc = std::min(grid_fv(h->n, 256, h->num_sms), h->num_sms * 6);
+    if (h->ell_w > 0 && h->ell_w <= 6)
+        k_fv_grad_cell_fl<6><<<gc, 256, 0, s>>>(h->n, h->at<int>(L.FL), t, p, bstart, blist, bface_sf, bface_type,
+                                                cell_v, grad);
+    else
+        k_fv_grad_cell<<<gc, 256, 0, s>>>(h->n, h->at<int>(L.lo_start), h->at<int>(L.lo_face),
+                                          h->at<int>(L.own_start), t, p, bstart, blist, bface_sf, bface_type, cell_v,
+                                          grad);
     count_launch();
     SPUMA_CUDA(cudaGetLastError());
     return SPUMA_OK;
@@ -397,9 +509,7 @@ spuma_status spuma_pressure_rhs(spuma_ldu_t h, const double* face_sf, const doub
     int *bstart, *blist;
     spuma_status st = boundary_lists(h, n_bfaces, bface_cell, &bstart, &blist, s);
     if (st != SPUMA_OK) return st;
-    k_fv_cell_sum<<<std::min(grid_fv(h->n, 256, h->num_sms), h->num_sms * 8), 256, 0, s>>>(
-        h->n, h->at<int>(L.lo_start), h->at<int>(L.lo_face), h->at<int>(L.own_start), dcp, bstart, blist, bphi, -1, b);
-    count_launch();
+    launch_cell_sum(h, dcp, bstart, blist, bphi, -1, b, s);
     SPUMA_CUDA(cudaGetLastError());
     return SPUMA_OK;
 }
@@ -445,9 +555,7 @@ spuma_status spuma_fv_div(spuma_ldu_t h, const double* phi, int32_t n_bfaces, co
     spuma_status st = boundary_lists(h, n_bfaces, bface_cell, &bstart, &blist, s);
     if (st != SPUMA_OK) return st;
     const Layout& L = h->L;
-    k_fv_cell_sum<<<std::min(grid_fv(h->n, 256, h->num_sms), h->num_sms * 8), 256, 0, s>>>(
-        h->n, h->at<int>(L.lo_start), h->at<int>(L.lo_face), h->at<int>(L.own_start), phi, bstart, blist, bphi, 1, div);
-    count_launch();
+    launch_cell_sum(h, phi, bstart, blist, bphi, 1, div, s);
     SPUMA_CUDA(cudaGetLastError());
     return SPUMA_OK;
 }

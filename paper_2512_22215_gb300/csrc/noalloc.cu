@@ -22,7 +22,7 @@ bool ctl_ok(const spuma_solver_controls* c);
 
 using namespace spuma;
 
-// 32 MiB: enough for hex meshes of about 70 thousand cells.  Every GPU that
+// 32 MiB: enough for hex meshes of about 65 thousand cells.  Every GPU that
 // loads the library holds this array until the process exits.
 constexpr size_t kStaticWorkspaceBytes = size_t(32) << 20;
 static __device__ __align__(256) unsigned char g_static_workspace[kStaticWorkspaceBytes];

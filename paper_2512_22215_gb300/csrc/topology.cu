@@ -71,6 +71,7 @@ Layout make_layout(int64_t n, int64_t nf, bool asym)
     // slots (no more than one padding slot per row on average)
     L.ell_slots = 2 * (size_t)nf + (size_t)n;
     L.Ecol = take(4 * L.ell_slots);
+    L.FL = take(4 * L.ell_slots);
     L.Ea64 = take(8 * L.ell_slots);
     L.Ea32 = take(4 * L.ell_slots);
     L.x64 = take(d8n);
@@ -482,6 +483,24 @@ __global__ void k_ell_fill(int n, size_t slots, const int* __restrict__ wptr, co
     }
 }
 
+// The cells' faces in the same fixed-width column-major form, in the caller's
+// (original) cell order, for the pressure-step operators: entry j of cell i
+// at j n + i, its neighbour-side faces (ascending) then its owner-side faces
+// (ascending), -(f + 1) for a face where i is the neighbour, f + 1 where it
+// is the owner, 0 past the cell's end.  The width is the Amul layout's (a
+// cell's face count is its row's entry count).
+__global__ void k_face_list_fill(int n, size_t slots, const int* __restrict__ wptr, const int* __restrict__ lo_start,
+                                 const int* __restrict__ lo_face, const int* __restrict__ own_start, int* FL)
+{
+    const int w = *wptr;
+    if (!ell_fits(w, n, slots)) return;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int k0 = lo_start[i], nl = lo_start[i + 1] - k0, f0 = own_start[i], nt = nl + own_start[i + 1] - f0;
+        for (int j = 0; j < w; j++)
+            FL[(size_t)j * n + i] = j < nl ? -(lo_face[k0 + j] + 1) : (j < nt ? f0 + (j - nl) + 1 : 0);
+    }
+}
+
 spuma_status scan_exclusive_ext(const int* in, int64_t n, int* out, int* tmp, cudaStream_t s)
 {
     return scan_exclusive(in, n, out, tmp, s);
@@ -710,7 +729,9 @@ spuma_status spuma_ldu_create_with_centres(int32_t n, int32_t nf, const int32_t*
         k_row_width<<<grid_for(n, T, h->num_sms), T, 0, s>>>(n, Lptr, Uptr, wdev);
         k_ell_fill<<<grid_for(n, T, h->num_sms), T, 0, s>>>(n, L.ell_slots, wdev, Lptr, h->at<int>(L.Lcol), Uptr,
                                                             h->at<int>(L.Ucol), h->at<int>(L.Ecol));
-        count_launch(2);
+        k_face_list_fill<<<grid_for(n, T, h->num_sms), T, 0, s>>>(n, L.ell_slots, wdev, lo_start, lo_face, own_start,
+                                                                  h->at<int>(L.FL));
+        count_launch(3);
         CU(cudaMemcpyAsync(&h->ell_w, wdev, sizeof(int), cudaMemcpyDeviceToHost, s));
         h->h_lvl.resize(nlev + 1);
         CU(cudaMemcpyAsync(h->h_lvl.data(), lvl, 4 * (size_t)(nlev + 1), cudaMemcpyDeviceToHost, s));
