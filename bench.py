@@ -199,9 +199,10 @@ def make_case(n: int, seed=None):
 def profile_run(args, local):
     """One launch of each hot kernel on the n^3 workload, in this order: the
     assembly, a mixed solve, an FP64 solve, the pressure-step operators
-    (weights, gradient, right-hand side, flux, divergence) and the stand-alone
-    FP64 and FP32 Amul on the prepared matrix.  For profiler captures (-k
-    selects the kernel); prints one line."""
+    (weights, gradient, right-hand side, flux, divergence), the stand-alone
+    FP64 and FP32 Amul on the prepared matrix, and a GAMG solve (two-stage
+    Gauss-Seidel, algebraic pairing).  For profiler captures (-k selects the
+    kernel); prints one line."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -231,9 +232,14 @@ def profile_run(args, local):
     xi = M.to_internal(b)
     M.amul_prepared(xi)
     M.amul_prepared(xi.float())
+    # GAMG with the two-stage Gauss-Seidel smoother on algebraic pairing weights
+    from paper_2512_22215_gb300 import GamgSolver
+    gs = GamgSolver(M, up.abs(), smoother=1)
+    _, pg = gs.solve(dg, up, b, None, SolverControls(tolerance=1e-8, max_iter=500))
     torch.cuda.synchronize()
     print(json.dumps({"profile_run": f"{args.n}^3", "cells": m.n_cells, "faces": m.n_faces,
-                      "mixed_iters": pm["n_iter"], "fp64_iters": pf["n_iter"]}), flush=True)
+                      "mixed_iters": pm["n_iter"], "fp64_iters": pf["n_iter"], "gamg_vcycles": pg["n_iter"]}),
+          flush=True)
 
 
 def cpu_sample(case, n_inner_sample: int):

@@ -166,8 +166,16 @@ __global__ void __launch_bounds__(256, 6) k_fv_grad_cell(int n, const int* __res
 // first, then its values in one gather round.
 __device__ __forceinline__ int fl_face(int v) { return v > 0 ? v - 1 : -v - 1; }
 
+// Exact negation (the sign bit flipped) when neg, on the integer pipe: GB300
+// issues FP64 instructions at a small fraction of its integer rate, and a
+// floating-point negation or select would take an FP64 issue slot.
+__device__ __forceinline__ double flip_sign(double q, bool neg)
+{
+    return __longlong_as_double(__double_as_longlong(q) ^ (neg ? (long long)0x8000000000000000ull : 0ll));
+}
+
 template <int W>
-__global__ void __launch_bounds__(256, 6) k_fv_grad_cell_fl(int n, const int* __restrict__ FL,
+__global__ void __launch_bounds__(256, 6) k_fv_grad_cell_fl(int n, int w, const int* __restrict__ FL,
                                                             const double4* __restrict__ t,
                                                             const double* __restrict__ p,
                                                             const int* __restrict__ bstart,
@@ -178,9 +186,9 @@ __global__ void __launch_bounds__(256, 6) k_fv_grad_cell_fl(int n, const int* __
 {
     constexpr int H = (W + 1) / 2;   // records gathered in two rounds of H (registers)
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int e[W];
+        int e[W];   // the list's width w <= W columns; the rest read as padding
 #pragma unroll
-        for (int j = 0; j < W; j++) e[j] = __ldcs(FL + (size_t)j * n + i);
+        for (int j = 0; j < W; j++) e[j] = j < w ? __ldcs(FL + (size_t)j * n + i) : 0;
         double gx = 0.0, gy = 0.0, gz = 0.0;
 #pragma unroll
         for (int h = 0; h < W; h += H) {
@@ -188,12 +196,8 @@ __global__ void __launch_bounds__(256, 6) k_fv_grad_cell_fl(int n, const int* __
 #pragma unroll
             for (int j = 0; j < H; j++) {
                 const int ej = h + j < W ? e[h + j] : 0;
-                if (ej != 0) {
-                    const double4 q = ld_t4(t, fl_face(ej));
-                    tv[j] = ej < 0 ? make_double4(-q.x, -q.y, -q.z, 0.0) : q;   // exact negation
-                } else {
-                    tv[j] = make_double4(0.0, 0.0, 0.0, 0.0);
-                }
+                const double4 q = ej != 0 ? ld_t4(t, fl_face(ej)) : make_double4(0.0, 0.0, 0.0, 0.0);
+                tv[j] = make_double4(flip_sign(q.x, ej < 0), flip_sign(q.y, ej < 0), flip_sign(q.z, ej < 0), 0.0);
             }
 #pragma unroll
             for (int j = 0; j < H; j++)
@@ -221,7 +225,7 @@ __global__ void __launch_bounds__(256, 6) k_fv_grad_cell_fl(int n, const int* __
 }
 
 template <int W>
-__global__ void __launch_bounds__(256, 8) k_fv_cell_sum_fl(int n, const int* __restrict__ FL,
+__global__ void __launch_bounds__(256, 8) k_fv_cell_sum_fl(int n, int w, const int* __restrict__ FL,
                                                            const double* __restrict__ val,
                                                            const int* __restrict__ bstart,
                                                            const int* __restrict__ blist,
@@ -229,14 +233,14 @@ __global__ void __launch_bounds__(256, 8) k_fv_cell_sum_fl(int n, const int* __r
                                                            double* __restrict__ out)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int e[W];
+        int e[W];   // the list's width w <= W columns; the rest read as padding
 #pragma unroll
-        for (int j = 0; j < W; j++) e[j] = __ldcs(FL + (size_t)j * n + i);
+        for (int j = 0; j < W; j++) e[j] = j < w ? __ldcs(FL + (size_t)j * n + i) : 0;
         double t[W];
 #pragma unroll
         for (int j = 0; j < W; j++) {
             const double q = e[j] != 0 ? __ldcs(val + fl_face(e[j])) : 0.0;
-            t[j] = e[j] < 0 ? -q : q;   // neighbour side subtracts (an exact negation)
+            t[j] = flip_sign(q, e[j] < 0);   // the neighbour side subtracts
         }
         double acc = 0.0;
 #pragma unroll
@@ -342,7 +346,7 @@ static void launch_cell_sum(spuma_ldu_t h, const double* val, const int* bstart,
     const Layout& L = h->L;
     const int g = std::min(grid_fv(h->n, 256, h->num_sms), h->num_sms * 8);
     if (h->ell_w > 0 && h->ell_w <= 6)
-        k_fv_cell_sum_fl<6><<<g, 256, 0, s>>>(h->n, h->at<int>(L.FL), val, bstart, blist, bphi, bsign, out);
+        k_fv_cell_sum_fl<6><<<g, 256, 0, s>>>(h->n, h->ell_w, h->at<int>(L.FL), val, bstart, blist, bphi, bsign, out);
     else
         k_fv_cell_sum<<<g, 256, 0, s>>>(h->n, h->at<int>(L.lo_start), h->at<int>(L.lo_face), h->at<int>(L.own_start),
                                         val, bstart, blist, bphi, bsign, out);
@@ -475,8 +479,8 @@ spuma_status spuma_fv_grad(spuma_ldu_t h, const double* face_sf, const double* w
     }
     const int gc = std::min(grid_fv(h->n, 256, h->num_sms), h->num_sms * 6);
     if (h->ell_w > 0 && h->ell_w <= 6)
-        k_fv_grad_cell_fl<6><<<gc, 256, 0, s>>>(h->n, h->at<int>(L.FL), t, p, bstart, blist, bface_sf, bface_type,
-                                                cell_v, grad);
+        k_fv_grad_cell_fl<6><<<gc, 256, 0, s>>>(h->n, h->ell_w, h->at<int>(L.FL), t, p, bstart, blist, bface_sf,
+                                                bface_type, cell_v, grad);
     else
         k_fv_grad_cell<<<gc, 256, 0, s>>>(h->n, h->at<int>(L.lo_start), h->at<int>(L.lo_face),
                                           h->at<int>(L.own_start), t, p, bstart, blist, bface_sf, bface_type, cell_v,
