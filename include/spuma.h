@@ -500,10 +500,13 @@ int32_t spuma_tune_cache_store(const char* path, const char* signature, int32_t 
  * into a table in the workspace (slots 0..63 forward DIC level L, 64..127
  * backward level L, 128 search direction, 129 Amul + p.Ap, 130 diagonal
  * pass, 132 FP64 refinement residual, 134 x/r update pass, 140 PCG
- * iterations); this copies the first n entries (synchronous).  Two more
- * variables change how later solves run, never what they compute:
- * SPUMA_FUSE_UPDATE=1 folds the x/r update into the forward DIC sweep, and
- * SPUMA_SOLVE_BLOCKS_PER_SM caps the solver's blocks per SM.               */
+ * iterations); this copies the first n entries (synchronous).  More
+ * variables change how later solves run, never what they compute (read once
+ * per process): SPUMA_SOLVE_BLOCKS_PER_SM caps the solver's blocks per SM,
+ * SPUMA_TAIL_ROWS sets the row limit of the small last DIC levels that the
+ * first block sweeps alone (0: none), and SPUMA_SWEEP=0 strides a level's
+ * rows over the blocks instead of giving each block one contiguous chunk of
+ * every level.                                                             */
 spuma_status spuma_read_phase_clocks(spuma_ldu_t h, int64_t* out, int32_t n, spuma_stream_t stream);
 const char* spuma_status_string(int32_t status);
 const char* spuma_last_error(void);

@@ -140,50 +140,6 @@ __device__ __forceinline__ bool group_sync(const Group& g)
     return s_err == 0;
 }
 
-// The same barrier in two halves, so that a block can work between its
-// arrival and its wait.  group_arrive: the block's threads meet, then thread 0
-// makes the acquire-release arrival and keeps the count to wait for (returned
-// to thread 0 only; ~0 when an error was already recorded).  group_wait: thread
-// 0 waits (bounded) for that count, the block meets again; false on error.
-__device__ __forceinline__ unsigned long long group_arrive(const Group& g)
-{
-    __syncthreads();
-    unsigned long long target = 0;
-    if (threadIdx.x == 0) {
-        const unsigned long long old = atom_add_acq_rel(g.word, 1ull);
-        const unsigned long long nb = (unsigned long long)g.nblocks;
-        target = (old & kErrBit) ? ~0ull : ((old & ~kErrBit) / nb + 1ull) * nb;
-    }
-    return target;
-}
-
-__device__ __forceinline__ bool group_wait(const Group& g, unsigned long long target)
-{
-    __shared__ int s_err2;
-    if (threadIdx.x == 0) {
-        bool err = target == ~0ull;
-        if (!err) {
-            const unsigned long long t0 = global_timer_ns();
-            for (;;) {
-                const unsigned long long w = ld_acquire(g.word);
-                if (w & kErrBit) {
-                    err = true;
-                    break;
-                }
-                if ((w & ~kErrBit) >= target) break;
-                if (global_timer_ns() - t0 > g.timeout_ns) {
-                    flag_error(g.status, SPUMA_ERR_DEVICE_TIMEOUT, g.bid);
-                    err = true;
-                    break;
-                }
-            }
-        }
-        s_err2 = err ? 1 : 0;
-    }
-    __syncthreads();
-    return s_err2 == 0;
-}
-
 // a = (gamma |S|) / max(n.d, 0.05 |d|), no contraction (bit-identical to the
 // sequential definition).
 __device__ __forceinline__ double face_coeff(double sx, double sy, double sz, double dx, double dy, double dz,
@@ -327,8 +283,6 @@ struct Layout {
     size_t partials, bar, status, args, clk;
     // cached per-cell boundary-face lists (pressure-step operators)
     size_t bstart, blist, blist_cap;
-    // per-row flags of the split-phase DIC sweeps
-    size_t loc;
     // asymmetric matrices (PBiCG), present when the workspace was sized with
     // SPUMA_WORKSPACE_ASYMMETRIC: A^T's coefficients in the internal CSR, the
     // transposed DILU sweep coefficients, the transposed search direction

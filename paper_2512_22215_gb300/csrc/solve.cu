@@ -435,7 +435,6 @@ __device__ __forceinline__ void vadd_abs(A& acc, double2 r)
 }
 // ------------------------------------------------------------ phases --------
 __device__ __forceinline__ void gather_symmetric(const SolveArgs& a, const RowIter& it, bool& bad);
-__device__ void classify_rows(const SolveArgs& a, const RowIter& it, int nblocks);
 
 // Gather the LDU coefficients into the internal layout (+ FP32 copies).
 template <bool ASYM>
@@ -464,7 +463,6 @@ __device__ bool phase_gather(const SolveArgs& a, const Group& g)
     } else {
         gather_symmetric(a, it, bad);
     }
-    if (a.sweep == 2 && a.loc) classify_rows(a, it, g.nblocks);
     if (bad) flag_error(a.status, SPUMA_ERR_NONFINITE, -1);
     return group_sync(g);
 }
@@ -581,22 +579,12 @@ __device__ bool phase_factor(const SolveArgs& a, const Group& g)
 // A template argument, so that the PCG kernels keep their own code.
 enum RhoWith { RHO_R = 0, RHO_VEC = 1, RHO_NONE = 2 };
 
-// Which rows of a level a sweep step takes: all of them (loc == NULL), or
-// only those whose flag bit `bit` equals `want` (the split-phase sweeps take
-// a level's block-local rows before the grid barrier's wait, the others after
-// it).
-struct RowFilter {
-    const unsigned char* loc;
-    int bit, want;
-    __device__ __forceinline__ bool take(int p) const { return !loc || (((loc[p] >> bit) & 1) == want); }
-};
-
 // Forward rows of one level: w = rD r - sum (rD a) w_lower (ascending face
 // order); with `rho` (top level: no upper neighbours, so w is final here)
 // also rho += w r (or w dotv).
 template <class T, int RW>
 __device__ __forceinline__ void fwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int r1, int first, int stride, bool rho,
-                                         const T* dotv, Acc<T>& arho, RowFilter rf = RowFilter{nullptr, 0, 0})
+                                         const T* dotv, Acc<T>& arho)
 {
     constexpr int R = ChainShape<T>::R, G = ChainShape<T>::G;
     for (int pb = r0 + first; pb < r1; pb += R * stride) {
@@ -606,7 +594,7 @@ __device__ __forceinline__ void fwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int
 #pragma unroll
         for (int k = 0; k < R; k++) {
             p[k] = pb + k * stride;
-            ok[k] = p[k] < r1 && rf.take(p[k]);
+            ok[k] = p[k] < r1;
             e0[k] = ok[k] ? __ldcs(A.Lptr + p[k]) : 0;
             e1[k] = ok[k] ? __ldcs(A.Lptr + p[k] + 1) : 0;
             rr[k] = ok[k] ? v.r[p[k]] : T(0);
@@ -626,7 +614,7 @@ __device__ __forceinline__ void fwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int
 // order); rho += w r (or w dotv).
 template <class T, int RW>
 __device__ __forceinline__ void bwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int r1, int first, int stride,
-                                         const T* dotv, Acc<T>& arho, RowFilter rf = RowFilter{nullptr, 0, 0})
+                                         const T* dotv, Acc<T>& arho)
 {
     constexpr int R = ChainShape<T>::R, G = ChainShape<T>::G;
     // row extents one round ahead: the next round's are loaded while this
@@ -646,7 +634,7 @@ __device__ __forceinline__ void bwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int
 #pragma unroll
         for (int k = 0; k < R; k++) {
             p[k] = pb + k * stride;
-            ok[k] = p[k] < r1 && rf.take(p[k]);
+            ok[k] = p[k] < r1;
             e0[k] = ok[k] ? e0n[k] : 0;
             e1[k] = ok[k] ? e1n[k] : 0;
             const int pn = pb + (R + k) * stride;
@@ -665,7 +653,7 @@ __device__ __forceinline__ void bwd_rows(const Mat<T>& A, Vecs<T> v, int r0, int
     }
 }
 
-// The block's contiguous chunk [c0, c1) of level L (sweep mappings 1, 2):
+// The block's contiguous chunk [c0, c1) of level L (sweep mapping 1):
 // the same 1/nblocks share of every level's Morton order, so a block's chunks
 // of consecutive levels cover nearly the same region of the mesh.
 __device__ __forceinline__ void level_chunk(const int* lvl, int L, int nblocks, int bid, int& c0, int& c1)
@@ -676,45 +664,6 @@ __device__ __forceinline__ void level_chunk(const int* lvl, int L, int nblocks, 
     c1 = min(c0 + chunk, r1);
 }
 
-// Flags of the split-phase sweeps, one byte per row, for the launch's group
-// size: bit 0, the row's lower neighbours in the level just below it all lie
-// in the chunk of that level that its own block sweeps (the row may go before
-// the grid barrier's wait in the forward sweep); bit 1, the same for its
-// upper neighbours in the level just above (backward sweep).
-__device__ void classify_rows(const SolveArgs& a, const RowIter& it, int nblocks)
-{
-    for (int p = it.first; p < a.n; p += it.stride) {
-        int lo = 0, hi = a.nlev;   // level: lvl[L] <= p < lvl[L + 1]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (a.lvl[mid] <= p) lo = mid; else hi = mid;
-        }
-        const int L = lo;
-        const int nL = a.lvl[L + 1] - a.lvl[L];
-        const int own = (p - a.lvl[L]) / ((nL + nblocks - 1) / nblocks);
-        unsigned char f = 0;
-        if (L >= 1) {
-            const int b0 = a.lvl[L - 1], b1 = a.lvl[L], ch = (b1 - b0 + nblocks - 1) / nblocks;
-            bool local = true;
-            for (int e = a.Lptr[p]; e < a.Lptr[p + 1]; e++) {
-                const int c = a.Lcol[e];
-                if (c >= b0 && c < b1 && (c - b0) / ch != own) local = false;
-            }
-            f |= local ? 1 : 0;
-        }
-        if (L + 1 < a.nlev) {
-            const int b0 = a.lvl[L + 1], b1 = a.lvl[L + 2], ch = (b1 - b0 + nblocks - 1) / nblocks;
-            bool local = true;
-            for (int e = a.Uptr[p]; e < a.Uptr[p + 1]; e++) {
-                const int c = a.Ucol[e];
-                if (c >= b0 && c < b1 && (c - b0) / ch != own) local = false;
-            }
-            f |= local ? 2 : 0;
-        }
-        a.loc[p] = f;
-    }
-}
-
 // w = M^-1 r with the DIC (or DILU) factor held in A's sweep coefficients,
 // and the block partials of rho (RhoWith) in `slot` before the last grid
 // barrier.  Forward sweep over levels 0 .. nlev-1, backward over nlev-2 .. 0
@@ -723,11 +672,10 @@ __device__ void classify_rows(const SolveArgs& a, const RowIter& it, int nblocks
 // barrier per level.  The small last levels (level >= tail_from) run on the
 // group's first block alone, forward then backward, with block-level
 // barriers and one grid barrier after them.
-// Row mapping (a.sweep): 0, the level's rows strided over the group in
-// blockDim-row pieces; 1, one contiguous chunk per block; 2, chunks with
-// split-phase barriers: after its rows of a level a block arrives, sweeps the
-// next level's rows whose neighbours in that level are all its own (flags of
-// classify_rows), and only then waits for the other blocks.
+// Row mapping (a.sweep): 1 (default), each block sweeps one contiguous chunk
+// of every level (the same 1/nblocks share of each level's Morton order);
+// 0, a level's rows strided over the group in blockDim-row pieces.  Measured
+// at 200^3: mixed solve 328.8 against 333.5 ms, FP64 582.5 against 599.7 ms.
 template <class T, int RW = RHO_R>
 __device__ bool dic_apply(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const Group& g, PhaseClock& pc,
                           const T* dotv = nullptr, int slot = SL_B)
@@ -736,68 +684,34 @@ __device__ bool dic_apply(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const 
     const int nlev = a.nlev, tail = min(a.tail_from, nlev);
     const int tid = (int)threadIdx.x, bs = (int)blockDim.x;
     Acc<T> arho;
-    auto store_rho = [&]() {
-        if (RW != RHO_NONE) {
+    auto end_step = [&](bool last) {
+        if (RW != RHO_NONE && last) {
             double t[1] = {arho.value()};
             block_reduce_store<1>(t, a.partials, slot, g.bid);
         }
-    };
-    auto end_step = [&](bool last) {
-        if (last) store_rho();
         return group_sync(g);
     };
     if (nlev == 0) return end_step(true);
-    const int mode = a.sweep;
-    const bool split = mode == 2 && a.loc;
-    unsigned long long tgt = 0;
-    bool pending = false;
-    auto level_rows = [&](bool fwd, int L, bool rho) {
-        int c0, c1;
-        if (mode == 0) {
+    const bool chunks = a.sweep != 0;
+    auto rows = [&](int L, int& c0, int& c1, int& first, int& stride) {
+        if (chunks) {
+            level_chunk(a.lvl, L, g.nblocks, g.bid, c0, c1);
+            first = tid;
+            stride = bs;
+        } else {
             c0 = a.lvl[L];
             c1 = a.lvl[L + 1];
-        } else {
-            level_chunk(a.lvl, L, g.nblocks, g.bid, c0, c1);
+            first = it.first;
+            stride = it.stride;
         }
-        const int first = mode == 0 ? it.first : tid, stride = mode == 0 ? it.stride : bs;
-        const int bit = fwd ? 0 : 1;
-        auto sweep = [&](RowFilter rf) {
-            if (fwd)
-                fwd_rows<T, RW>(A, v, c0, c1, first, stride, rho, dotv, arho, rf);
-            else
-                bwd_rows<T, RW>(A, v, c0, c1, first, stride, dotv, arho, rf);
-        };
-        if (split && pending) {
-            sweep(RowFilter{a.loc, bit, 1});            // this block's own: before the wait
-            const bool ok = group_wait(g, tgt);
-            pending = false;
-            if (!ok) return false;
-            sweep(RowFilter{a.loc, bit, 0});            // the others: after it
-        } else {
-            sweep(RowFilter{nullptr, 0, 0});
-        }
-        return true;
-    };
-    auto level_end = [&](bool last) {
-        if (last) store_rho();
-        if (split) {
-            tgt = group_arrive(g);
-            pending = true;
-            return true;
-        }
-        return group_sync(g);
-    };
-    auto settle = [&]() {
-        if (!pending) return true;
-        pending = false;
-        return group_wait(g, tgt);
     };
     for (int L = 0; L < tail; L++) {
-        if (!level_rows(true, L, L == nlev - 1)) return false;
-        if (!level_end(nlev == 1)) return false;
+        int c0, c1, first, stride;
+        rows(L, c0, c1, first, stride);
+        fwd_rows<T, RW>(A, v, c0, c1, first, stride, L == nlev - 1, dotv, arho);
+        if (!end_step(nlev == 1)) return false;
         pc.lap(CK_FWD + min(L, 63));
     }
-    if (!settle()) return false;
     if (tail < nlev) {
         if (g.bid == 0) {
             for (int L = tail; L < nlev; L++) {
@@ -813,11 +727,13 @@ __device__ bool dic_apply(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const 
         pc.lap(CK_FWD + min(tail, 63));
     }
     for (int L = min(tail, nlev - 1) - 1; L >= 0; L--) {
-        if (!level_rows(false, L, true)) return false;
-        if (!level_end(L == 0)) return false;
+        int c0, c1, first, stride;
+        rows(L, c0, c1, first, stride);
+        bwd_rows<T, RW>(A, v, c0, c1, first, stride, dotv, arho);
+        if (!end_step(L == 0)) return false;
         pc.lap(CK_BWD + min(L, 63));
     }
-    return settle();
+    return true;
 }
 
 // ----------------------------------------------------- streaming passes ---
@@ -1377,9 +1293,7 @@ __device__ void run_system(const SolveArgs& a, const Group& g)
         if (ok) {
             if (a.precond == SPUMA_PRECOND_DIC) {
                 PhaseClock pc(nullptr, g.bid);
-                SolveArgs b = a;
-                b.sweep = 0;   // no classification in this launch: the strided mapping
-                ok = dic_apply<double>(b, A, v, g, pc);
+                ok = dic_apply<double>(a, A, v, g, pc);
             } else {
                 for (int p = it.first; p < a.n; p += it.stride)
                     a.w[p] = a.precond == SPUMA_PRECOND_DIAGONAL ? __dmul_rn(a.rD64[p], a.r[p]) : a.r[p];
@@ -1557,14 +1471,13 @@ __global__ void k_read_rD(int n, const int* __restrict__ perm, const double* __r
 }
 
 // ------------------------------------------------------------ host side -----
-// Row mapping of the DIC sweeps (SPUMA_SWEEP: 0 strided, 1 contiguous chunks,
-// 2 chunks with split-phase barriers).
+// Row mapping of the DIC sweeps: 1 (default) contiguous level chunks per
+// block, 0 strided (SPUMA_SWEEP=0, a measurement override).
 static int sweep_mode()
 {
     static const int m = [] {
         const char* e = getenv("SPUMA_SWEEP");
-        const int v = e ? atoi(e) : 0;
-        return (v >= 0 && v <= 2) ? v : 0;
+        return (e && atoi(e) == 0) ? 0 : 1;
     }();
     return m;
 }
@@ -1622,7 +1535,6 @@ SolveArgs make_args(spuma_ldu_t h)
     a.partials = h->at<double>(L.partials);
     a.bar = h->at<unsigned>(L.bar);
     a.status = h->at<int>(L.status);
-    a.loc = h->at<unsigned char>(L.loc);
     a.sweep = sweep_mode();
     return a;
 }

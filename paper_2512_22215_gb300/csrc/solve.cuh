@@ -43,8 +43,7 @@ struct SolveArgs {
     int* status;
     spuma_solver_perf* perf;
     long long* phase_clk;  // optional per-phase SM-clock totals of group block 0 (diagnostics)
-    unsigned char* loc;    // per-row flags of the split-phase sweeps (bit 0 forward-local, bit 1 backward-local)
-    int sweep;             // DIC sweep mapping: 0 strided, 1 contiguous chunks, 2 chunks + split-phase barriers
+    int sweep;             // DIC sweep row mapping: 1 contiguous level chunks per block, 0 strided
 };
 
 struct BatchTable {

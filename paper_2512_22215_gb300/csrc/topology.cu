@@ -95,8 +95,6 @@ Layout make_layout(int64_t n, int64_t nf, bool asym)
     L.bstart = take(i4n1);
     L.blist_cap = 2 * (size_t)n;
     L.blist = take(4 * L.blist_cap);
-    // per-row flags of the split-phase DIC sweeps (one byte per row)
-    L.loc = take((size_t)n);
     if (asym) {
         L.asym = true;
         L.LaT64 = take(d8f);
