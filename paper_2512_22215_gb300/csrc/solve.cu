@@ -789,25 +789,43 @@ __device__ bool amul_sigma(const SolveArgs& a, const Mat<T>& A, Vecs<T> v, const
     constexpr int R = AmulShape<T>::R, G = AmulShape<T>::G;
     Acc<T> asig;
     RowIter it = rows_of(g);
-    if (PipeShape<T>::in_solver && A.ell_w > 0 && A.ell_w <= PipeShape<T>::G) {
-        ell_amul_pipelined<T, PipeShape<T>::R, PipeShape<T>::G>(A, v.p, it.first, it.stride, a.n,
-                                                                [&](int p, T y, T xp) {
-                                                                    v.q[p] = y;
-                                                                    asig.prod(y, xp);
-                                                                });
-    } else
-    for (int pb = it.first; pb < a.n; pb += R * it.stride) {
-        int p[R];
-        T y[R], pp[R];
+    // rows [r0, r1) from `first` with `stride`
+    auto range = [&](int r0, int r1, int first, int stride) {
+        if (PipeShape<T>::in_solver && A.ell_w > 0 && A.ell_w <= PipeShape<T>::G) {
+            ell_amul_pipelined<T, PipeShape<T>::R, PipeShape<T>::G>(A, v.p, r0 + first, stride, r1,
+                                                                    [&](int p, T y, T xp) {
+                                                                        v.q[p] = y;
+                                                                        asig.prod(y, xp);
+                                                                    });
+            return;
+        }
+        for (int pb = r0 + first; pb < r1; pb += R * stride) {
+            int p[R];
+            T y[R], pp[R];
 #pragma unroll
-        for (int k = 0; k < R; k++) p[k] = pb + k * it.stride;
-        amul_rows<T, R, G>(A, v.p, p, a.n, y, pp);
+            for (int k = 0; k < R; k++) p[k] = pb + k * stride;
+            amul_rows<T, R, G>(A, v.p, p, r1, y, pp);
 #pragma unroll
-        for (int k = 0; k < R; k++)
-            if (p[k] < a.n) {
-                v.q[p[k]] = y[k];
-                asig.prod(y[k], pp[k]);
-            }
+            for (int k = 0; k < R; k++)
+                if (p[k] < r1) {
+                    v.q[p[k]] = y[k];
+                    asig.prod(y[k], pp[k]);
+                }
+        }
+    };
+    // with amul_chunks each block takes its contiguous chunk of every level,
+    // as in the sweeps: the rows a block takes cover one region of the mesh in
+    // all levels, so the repeated gathers of a value stay in its SM's L1;
+    // otherwise one segment, all rows strided over the group
+    const int nseg = a.amul_chunks ? a.nlev : 1;
+    for (int L = 0; L < nseg; L++) {
+        int c0 = 0, c1 = a.n, first = it.first, stride = it.stride;
+        if (a.amul_chunks) {
+            level_chunk(a.lvl, L, g.nblocks, g.bid, c0, c1);
+            first = (int)threadIdx.x;
+            stride = (int)blockDim.x;
+        }
+        range(c0, c1, first, stride);
     }
     double sacc[1] = {asig.value()};
     block_reduce_store<1>(sacc, a.partials, SL_C, g.bid);
@@ -1647,6 +1665,11 @@ spuma_status launch_solve(spuma_ldu_t h, const SolveArgs& a, int threads, cudaSt
     unsigned long long tns = barrier_timeout_ns();
     SolveArgs b = a;
     b.tail_from = tail_level(h, threads);
+    // the Amul phase walks level chunks when the levels are wide (an average
+    // level gives every block at least a block's worth of rows)
+    static const bool amul_chunks_env = getenv("SPUMA_AMUL_CHUNKS") && atoi(getenv("SPUMA_AMUL_CHUNKS")) != 0;
+    b.amul_chunks = amul_chunks_env && b.sweep != 0 && h->nlev > 0 &&
+                    (int64_t)h->n / h->nlev >= (int64_t)grid * threads;
     if (getenv("SPUMA_PHASE_CLOCKS")) {
         b.phase_clk = h->at<long long>(h->L.clk);
         SPUMA_CUDA(cudaMemsetAsync(b.phase_clk, 0, 8 * 256, s));

@@ -44,6 +44,7 @@ struct SolveArgs {
     spuma_solver_perf* perf;
     long long* phase_clk;  // optional per-phase SM-clock totals of group block 0 (diagnostics)
     int sweep;             // DIC sweep row mapping: 1 contiguous level chunks per block, 0 strided
+    int amul_chunks;       // the Amul phase walks each block's chunk of every level (levels wide enough)
 };
 
 struct BatchTable {
