@@ -504,9 +504,10 @@ int32_t spuma_tune_cache_store(const char* path, const char* signature, int32_t 
  * variables change how later solves run, never what they compute (read once
  * per process): SPUMA_SOLVE_BLOCKS_PER_SM caps the solver's blocks per SM,
  * SPUMA_TAIL_ROWS sets the row limit of the small last DIC levels that the
- * first block sweeps alone (0: none), and SPUMA_SWEEP=0 strides a level's
+ * first block sweeps alone (0: none), SPUMA_SWEEP=0 strides a level's
  * rows over the blocks instead of giving each block one contiguous chunk of
- * every level.                                                             */
+ * every level, and SPUMA_AMUL_CHUNKS=1 makes the PCG's Amul phase walk those
+ * chunks too (on meshes whose levels are wide).                            */
 spuma_status spuma_read_phase_clocks(spuma_ldu_t h, int64_t* out, int32_t n, spuma_stream_t stream);
 const char* spuma_status_string(int32_t status);
 const char* spuma_last_error(void);
