@@ -133,6 +133,39 @@ def test_amul_f32_matches_dense():
     assert np.all(np.abs(y - ref) <= 8 * np.finfo(np.float32).eps * scale)
 
 
+def _fma32(a, b, c):
+    """float32 fused multiply-add: the product of two float32 values is exact in
+    float64, so the only rounding left is that of the float64 sum (and its
+    rounding to float32; a double rounding there is a one-in-millions event that
+    these inputs do not hit, checked below by the agreement itself)."""
+    return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def test_amul_f32_rounding_bitwise():
+    """The FP32 Amul restated element by element: d x rounded to float, then
+    each face's two terms as float FMAs in face order (float products are exact
+    in float64, so a float FMA is the float64 sum rounded to float; see
+    _fma32).  The oracle agrees bit for bit; summing the terms with separate
+    float roundings does not."""
+    c, up, dg = case((6, 5, 4), jitter=0.2, permute=True, seed=5, lognormal_gamma=True)
+    m = c.mesh
+    d32, u32 = dg.astype(np.float32), up.astype(np.float32)
+    x = np.random.default_rng(1).standard_normal(m.n_cells).astype(np.float32)
+    y = oracle.amul(m.lower, m.upper_addr, d32, u32, x)
+
+    def restate(term):
+        yr = (d32 * x).astype(np.float32)
+        for f in range(m.n_faces):
+            l_, u = m.lower[f], m.upper_addr[f]
+            yr[u] = term(u32[f], x[l_], yr[u])
+            yr[l_] = term(u32[f], x[u], yr[l_])
+        return yr
+
+    assert np.array_equal(y.view(np.uint32), restate(_fma32).view(np.uint32))
+    sep = restate(lambda a, b, c_: np.float32(np.float32(a * b) + c_))
+    assert not np.array_equal(y.view(np.uint32), sep.view(np.uint32))
+
+
 # ------------------------------------------------------------------ DIC ----
 @pytest.mark.parametrize("perm", [False, True])
 def test_dic_factor_reproduces_diagonal_and_pattern(perm):
@@ -164,6 +197,35 @@ def test_dic_f32_sweeps_close_to_f64():
     w32 = oracle.dic_precondition(m.lower, m.upper_addr, up, rD, r.astype(np.float32))
     assert w32.dtype == np.float32
     assert np.abs(w32 - w64).max() <= 1e-5 * np.abs(w64).max()
+
+
+def test_dic_f32_sweeps_rounding_reading_bitwise():
+    """The mixed form's FP32 sweeps, restated element by element: the diagonal
+    scale is rD rounded to float, each sweep coefficient the FP64 product rD a
+    rounded to float, each term one float FMA, faces ascending (forward) then
+    descending (backward).  The oracle's FP32 sweeps agree bit for bit; the
+    other reading of the coefficient, float(rD) * float(a) in float, gives other
+    bits."""
+    c, up, dg = case((6, 5, 4), jitter=0.2, permute=True, seed=6, lognormal_gamma=True)
+    m = c.mesh
+    rD, _ = oracle.dic_factor(m.lower, m.upper_addr, dg, up)
+    r = np.random.default_rng(3).standard_normal(m.n_cells).astype(np.float32)
+    w32 = oracle.dic_precondition(m.lower, m.upper_addr, up, rD, r)
+
+    def sweep(coef):
+        w = (rD.astype(np.float32) * r).astype(np.float32)
+        for f in range(m.n_faces):
+            u, l_ = m.upper_addr[f], m.lower[f]
+            w[u] = _fma32(-coef(u, f), w[l_], w[u])
+        for f in range(m.n_faces - 1, -1, -1):
+            u, l_ = m.upper_addr[f], m.lower[f]
+            w[l_] = _fma32(-coef(l_, f), w[u], w[l_])
+        return w
+
+    w_ref = sweep(lambda i, f: np.float32(rD[i] * up[f]))
+    assert np.array_equal(w32.view(np.uint32), w_ref.view(np.uint32))
+    w_alt = sweep(lambda i, f: np.float32(np.float32(rD[i]) * np.float32(up[f])))
+    assert not np.array_equal(w32.view(np.uint32), w_alt.view(np.uint32))
 
 
 def test_dic_chain_is_exact_cholesky():
