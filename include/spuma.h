@@ -389,7 +389,12 @@ spuma_status spuma_pbicg_solve(spuma_ldu_t h, const double* diag, const double* 
  *   e_i = fma(omega/d_i, r_i - (A e)_i, e_i), omega = 2/3.  x in/out (initial
  *   guess), original order; perf as spuma_pcg_solve (n_levels = GAMG levels).
  *   The hierarchy's handle h must outlive the GAMG object; its status and
- *   barrier words are shared with h's other calls (stream-ordered).
+ *   barrier words are shared with h's other calls (stream-ordered).  With
+ *   two or more levels, level 0 runs in h's internal (DIC level) order: its
+ *   coefficients are gathered into h's FP64 matrix region, so a matrix
+ *   prepared on h before (spuma_matrix_prepare) must be prepared again before
+ *   spuma_amul_prepared or spuma_precondition (spuma_precondition returns
+ *   SPUMA_ERR_INVALID_ARG until then; spuma_pcg_solve prepares its own).
  * ---------------------------------------------------------------------- */
 /* spuma_gamg_set_options: the smoother of later solves, SPUMA_GAMG_RICHARDSON
  *   (default; damped Jacobi as above) or SPUMA_GAMG_GAUSS_SEIDEL_2STAGE (the

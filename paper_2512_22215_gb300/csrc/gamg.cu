@@ -58,7 +58,22 @@ struct GamgLevel {
     double *r, *e, *q, *y;                  // right-hand side, correction, scratch, first-stage vector
 };
 
+// Level 0 in the mesh handle's internal order (rows grouped by DIC level,
+// Morton order inside a level): the solver's internal CSR (lower entries,
+// then upper, each in face order) and, when the mesh has it, its fixed-width
+// Amul layout, their coefficients gathered from the caller's arrays at the
+// start of each solve; the aggregation lists mapped to internal positions at
+// bind.  Every row sum keeps its face order, so the results are those of the
+// original-order level.  Used when the hierarchy has more than one level.
+struct GamgLvl0 {
+    int on, n, ell_w;
+    const int *perm, *Lptr, *Lcol, *Lface, *Uptr, *Ucol, *Uface, *Ecol;
+    double *La, *Ua, *d, *Ea;             // the handle's matrix region, filled per solve
+    const int *agg_int, *ccell_int;       // agg[perm[p]], iperm[ccell[j]]
+};
+
 struct GamgArgs {
+    GamgLvl0 z;
     int nlev, small_from;
     const GamgLevel* lv;                    // device array [nlev]
     const double* b_orig;
@@ -140,9 +155,84 @@ __device__ __forceinline__ double gamg_amul_row(const GamgLevel& L, const double
     return y;
 }
 
+// (A_0 x)_p in internal order: d_p x_p, then the row's entries in face order
+// (fixed-width layout, or lower then upper CSR entries), one FMA each; entry
+// loads grouped, then the gathers, then the FMAs in order.
+__device__ __forceinline__ double lvl0_amul_row(const GamgLvl0& z, const double* x, int p)
+{
+    double y = __dmul_rn(z.d[p], x[p]);
+    if (z.ell_w > 0) {
+        for (int j0 = 0; j0 < z.ell_w; j0 += 6) {
+            int c[6];
+            double v[6], xv[6];
+#pragma unroll
+            for (int j = 0; j < 6; j++) {
+                const bool ok = j0 + j < z.ell_w;
+                const size_t e = (size_t)(j0 + j) * z.n + p;
+                c[j] = ok ? __ldcs(z.Ecol + e) : -1;
+                v[j] = ok ? __ldcs(z.Ea + e) : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < 6; j++) xv[j] = c[j] >= 0 ? x[c[j]] : 0.0;
+#pragma unroll
+            for (int j = 0; j < 6; j++)
+                if (c[j] >= 0) y = __fma_rn(v[j], xv[j], y);
+        }
+        return y;
+    }
+    for (int e = z.Lptr[p]; e < z.Lptr[p + 1]; e++) y = __fma_rn(z.La[e], x[z.Lcol[e]], y);
+    for (int e = z.Uptr[p]; e < z.Uptr[p + 1]; e++) y = __fma_rn(z.Ua[e], x[z.Ucol[e]], y);
+    return y;
+}
+
+// A level's row operations, in internal order at level 0 when z.on.
+__device__ __forceinline__ double level_amul_row(const GamgArgs& a, int k, const double* x, int i)
+{
+    if (k == 0 && a.z.on) return lvl0_amul_row(a.z, x, i);
+    return gamg_amul_row(a.lv[k], a.lv[k].diag, x, i);
+}
+
+// s - sum over the row's lower entries (face order) of a_f y_col, one FMA each
+// (the two-stage Gauss-Seidel's second stage).
+__device__ __forceinline__ double level_lower_sweep(const GamgArgs& a, int k, const double* y, int i, double s)
+{
+    if (k == 0 && a.z.on) {
+        for (int e = a.z.Lptr[i]; e < a.z.Lptr[i + 1]; e++) s = __fma_rn(-a.z.La[e], y[a.z.Lcol[e]], s);
+        return s;
+    }
+    const GamgLevel& L = a.lv[k];
+    for (int e = L.rptr[i]; e < L.rptr[i + 1]; e++) {
+        const int c = L.rcol[e];
+        if (c < i) s = __fma_rn(-L.rval[e], y[c], s);
+    }
+    return s;
+}
+
+// Level 0's coefficients in internal order (per solve): the CSR entries, the
+// diagonal and the fixed-width layout, from the caller's (original) arrays.
+__device__ void lvl0_gather(const GamgArgs& a, int first, int stride)
+{
+    const GamgLvl0& z = a.z;
+    const GamgLevel& L0 = a.lv[0];
+    for (int e = first; e < L0.nf; e += stride) {
+        z.La[e] = L0.upper[z.Lface[e]];
+        z.Ua[e] = L0.upper[z.Uface[e]];
+    }
+    for (int p = first; p < z.n; p += stride) {
+        z.d[p] = L0.diag[z.perm[p]];
+        if (z.ell_w > 0) {
+            const int l0 = z.Lptr[p], nl = z.Lptr[p + 1] - l0, u0 = z.Uptr[p], nt = nl + z.Uptr[p + 1] - u0;
+            for (int j = 0; j < z.ell_w; j++)
+                z.Ea[(size_t)j * z.n + p] =
+                    j < nl ? L0.upper[z.Lface[l0 + j]] : (j < nt ? L0.upper[z.Uface[u0 + j - nl]] : 0.0);
+        }
+    }
+}
+
 // Galerkin coarse matrices level by level, then omega/diag on every level.
 __device__ bool gamg_coarse_matrices(const GamgArgs& a, const Group& g)
 {
+    if (a.z.on) lvl0_gather(a, g.bid * (int)blockDim.x + (int)threadIdx.x, g.nblocks * (int)blockDim.x);
     for (int k = 0; k + 1 < a.nlev; k++) {
         const GamgLevel& F = a.lv[k];
         const Exec x = exec_for(a, k + 1, g);
@@ -167,9 +257,12 @@ __device__ bool gamg_coarse_matrices(const GamgArgs& a, const Group& g)
     const int first = g.bid * (int)blockDim.x + (int)threadIdx.x, stride = g.nblocks * (int)blockDim.x;
     for (int k = 0; k < a.nlev; k++) {
         const GamgLevel& L = a.lv[k];
+        const bool z0 = k == 0 && a.z.on;
+        const double* dg = z0 ? a.z.d : L.diag;
         for (int i = first; i < L.n; i += stride)
-            L.wrd[i] = a.smoother == 1 ? __ddiv_rn(1.0, L.diag[i]) : __dmul_rn(kGamgOmega, __ddiv_rn(1.0, L.diag[i]));
-        for (int e = first; e < 2 * L.nf; e += stride) L.rval[e] = L.upper[L.rfac[e]];
+            L.wrd[i] = a.smoother == 1 ? __ddiv_rn(1.0, dg[i]) : __dmul_rn(kGamgOmega, __ddiv_rn(1.0, dg[i]));
+        if (!z0)
+            for (int e = first; e < 2 * L.nf; e += stride) L.rval[e] = L.upper[L.rfac[e]];
     }
     if (!group_sync(g)) return false;
     // DIC factor of the coarsest matrix by one thread, rows ascending: p_i =
@@ -294,10 +387,11 @@ __device__ bool gamg_vcycle(const GamgArgs& a, const Group& g)
         const GamgLevel& F = a.lv[k];
         const GamgLevel& C = a.lv[k + 1];
         const Exec x = exec_for(a, k + 1, g);
+        const int* cc = k == 0 && a.z.on ? a.z.ccell_int : F.ccell;
         if (x.active)
             for (int c = x.first; c < C.n; c += x.stride) {
                 double s = 0.0;
-                for (int j = F.cptr[c]; j < F.cptr[c + 1]; j++) s = __dadd_rn(s, F.r[F.ccell[j]]);
+                for (int j = F.cptr[c]; j < F.cptr[c + 1]; j++) s = __dadd_rn(s, F.r[cc[j]]);
                 C.r[c] = s;
             }
         if (!exec_sync(x, g)) return false;
@@ -309,13 +403,14 @@ __device__ bool gamg_vcycle(const GamgArgs& a, const Group& g)
         const GamgLevel& C = a.lv[k + 1];
         if (k + 1 == a.small_from && !group_sync(g)) return false;   // the first block's levels are done
         const Exec x = exec_for(a, k, g);
+        const int* ag = k == 0 && a.z.on ? a.z.agg_int : L.agg;
         if (x.active)
-            for (int i = x.first; i < L.n; i += x.stride) L.e[i] = C.e[L.agg[i]];
+            for (int i = x.first; i < L.n; i += x.stride) L.e[i] = C.e[ag[i]];
         if (!exec_sync(x, g)) return false;
         double v[2] = {0.0, 0.0};
         if (x.active)
             for (int i = x.first; i < L.n; i += x.stride) {
-                const double qi = gamg_amul_row(L, L.diag, L.e, i);
+                const double qi = level_amul_row(a, k, L.e, i);
                 v[0] = __fma_rn(L.e[i], L.r[i], v[0]);
                 v[1] = __fma_rn(L.e[i], qi, v[1]);
             }
@@ -332,18 +427,14 @@ __device__ bool gamg_vcycle(const GamgArgs& a, const Group& g)
             for (int s = 0; s < kGamgPostSweeps; s++) {
                 if (x.active)
                     for (int i = x.first; i < L.n; i += x.stride) {
-                        const double qi = __dsub_rn(L.r[i], gamg_amul_row(L, L.diag, L.e, i));
+                        const double qi = __dsub_rn(L.r[i], level_amul_row(a, k, L.e, i));
                         L.q[i] = qi;
                         L.y[i] = __dmul_rn(L.wrd[i], qi);
                     }
                 if (!exec_sync(x, g)) return false;
                 if (x.active)
                     for (int i = x.first; i < L.n; i += x.stride) {
-                        double si = L.q[i];
-                        for (int e = L.rptr[i]; e < L.rptr[i + 1]; e++) {
-                            const int c = L.rcol[e];
-                            if (c < i) si = __fma_rn(-L.rval[e], L.y[c], si);
-                        }
+                        const double si = level_lower_sweep(a, k, L.y, i, L.q[i]);
                         L.e[i] = __dadd_rn(L.e[i], __dmul_rn(L.wrd[i], si));
                     }
                 if (!exec_sync(x, g)) return false;
@@ -356,7 +447,7 @@ __device__ bool gamg_vcycle(const GamgArgs& a, const Group& g)
                 double* dst = (s & 1) ? L.e : L.q;
                 if (x.active)
                     for (int i = x.first; i < L.n; i += x.stride)
-                        dst[i] = __fma_rn(L.wrd[i], __dsub_rn(L.r[i], gamg_amul_row(L, L.diag, src, i)), src[i]);
+                        dst[i] = __fma_rn(L.wrd[i], __dsub_rn(L.r[i], level_amul_row(a, k, src, i)), src[i]);
                 if (!exec_sync(x, g)) return false;
             }
         }
@@ -377,12 +468,14 @@ __global__ void __launch_bounds__(1024, 1) k_gamg(GamgArgs a, unsigned long long
     bool ok = gamg_coarse_matrices(a, g);
     // x, b, r = b - A x, normFactor (row sums of A times mean(x)), res0
     double v[1] = {0.0};
+    const bool z0 = a.z.on;   // level 0 (x, b, r) in internal order
     if (ok) {
         for (int i = it.first; i < L0.n; i += it.stride) {
-            a.x[i] = a.x_orig[i];
-            a.b[i] = a.b_orig[i];
-            v[0] += a.x[i];
-            if (!isfinite(a.b[i])) flag_error(a.status, SPUMA_ERR_NONFINITE, i);
+            const int o = z0 ? a.z.perm[i] : i;
+            a.x[i] = a.x_orig[o];
+            a.b[i] = a.b_orig[o];
+            v[0] += a.x_orig[i];
+            if (!isfinite(a.b_orig[i])) flag_error(a.status, SPUMA_ERR_NONFINITE, i);
         }
         block_reduce_store<1>(v, a.partials, GS_A, g.bid);
         ok = group_sync(g);
@@ -394,11 +487,18 @@ __global__ void __launch_bounds__(1024, 1) k_gamg(GamgArgs a, unsigned long long
         const double xbar = L0.n > 0 ? t[0] / (double)L0.n : 0.0;
         double acc[2] = {0.0, 0.0};
         for (int i = it.first; i < L0.n; i += it.stride) {
-            const double q = gamg_amul_row(L0, L0.diag, a.x, i);
+            const double q = level_amul_row(a, 0, a.x, i);
             const double r = a.b[i] - q;
             a.res[i] = r;
-            double s = L0.diag[i];
-            for (int e = L0.rptr[i]; e < L0.rptr[i + 1]; e++) s += L0.rval[e];
+            double s;
+            if (z0) {
+                s = a.z.d[i];
+                for (int e = a.z.Lptr[i]; e < a.z.Lptr[i + 1]; e++) s += a.z.La[e];
+                for (int e = a.z.Uptr[i]; e < a.z.Uptr[i + 1]; e++) s += a.z.Ua[e];
+            } else {
+                s = L0.diag[i];
+                for (int e = L0.rptr[i]; e < L0.rptr[i + 1]; e++) s += L0.rval[e];
+            }
             const double tt = s * xbar;
             acc[0] += fabs(r);
             acc[1] += fabs(q - tt) + fabs(a.b[i] - tt);
@@ -423,7 +523,7 @@ __global__ void __launch_bounds__(1024, 1) k_gamg(GamgArgs a, unsigned long long
             ok = group_sync(g);
             if (!ok) break;
             for (int i = it.first; i < L0.n; i += it.stride) {
-                const double r = a.b[i] - gamg_amul_row(L0, L0.diag, a.x, i);
+                const double r = a.b[i] - level_amul_row(a, 0, a.x, i);
                 a.res[i] = r;
                 acc[0] += fabs(r);
             }
@@ -440,7 +540,7 @@ __global__ void __launch_bounds__(1024, 1) k_gamg(GamgArgs a, unsigned long long
     if (ok) {
         double acc[2] = {0.0, 0.0};
         for (int i = it.first; i < L0.n; i += it.stride) {
-            const double r = __dsub_rn(a.b[i], gamg_amul_row(L0, L0.diag, a.x, i));
+            const double r = __dsub_rn(a.b[i], level_amul_row(a, 0, a.x, i));
             acc[0] = __fma_rn(r, r, acc[0]);
             acc[1] = __fma_rn(a.b[i], a.b[i], acc[1]);
         }
@@ -453,7 +553,7 @@ __global__ void __launch_bounds__(1024, 1) k_gamg(GamgArgs a, unsigned long long
         }
     }
     if (ok)
-        for (int i = it.first; i < L0.n; i += it.stride) a.x_orig[i] = a.x[i];
+        for (int i = it.first; i < L0.n; i += it.stride) a.x_orig[z0 ? a.z.perm[i] : i] = a.x[i];
     if (g.bid == 0 && threadIdx.x == 0 && a.perf) {
         pf.initial_residual = res0;
         pf.final_residual = res;
@@ -464,6 +564,18 @@ __global__ void __launch_bounds__(1024, 1) k_gamg(GamgArgs a, unsigned long long
         if (!ok && pf.status == 0) pf.status = SPUMA_ERR_DEVICE_TIMEOUT;
         if (pf.status != 0) pf.converged = 0;
         *a.perf = pf;
+    }
+}
+
+// Level 0's aggregation lists at internal positions: agg_int[p] = agg[perm[p]],
+// ccell_int[j] = iperm[ccell[j]].
+__global__ void k_gamg_lvl0_maps(int n, const int* __restrict__ perm, const int* __restrict__ iperm,
+                                 const int* __restrict__ agg, const int* __restrict__ ccell, int* agg_int,
+                                 int* ccell_int)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        agg_int[p] = agg[perm[p]];
+        ccell_int[p] = iperm[ccell[p]];
     }
 }
 
@@ -542,6 +654,7 @@ struct spuma_gamg {
     double *x = nullptr, *b = nullptr, *pw = nullptr, *pp = nullptr, *pq = nullptr, *px = nullptr;
     double* crD = nullptr;
     double* partials = nullptr;
+    int *agg_int = nullptr, *ccell_int = nullptr;   // level 0 in internal order (two or more levels)
     int small_from = 0;
     int smoother = 0;                      // 0 Richardson, 1 two-stage Gauss-Seidel
     int coarsest_precond = SPUMA_PRECOND_DIAGONAL;
@@ -601,6 +714,11 @@ size_t gamg_layout(spuma_gamg& G, bool assign)
     G.px = (double*)take(8 * nc + 8);
     G.crD = (double*)take(8 * nc + 8);
     G.partials = (double*)take(8 * (size_t)kMaxBlocks * kSlots);
+    G.agg_int = G.ccell_int = nullptr;
+    if (L >= 2) {
+        G.agg_int = (int*)take(4 * n0 + 4);
+        G.ccell_int = (int*)take(4 * n0 + 4);
+    }
     return off;
 }
 
@@ -644,32 +762,56 @@ spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_s
         GamgHostLevel& F = G->lv.back();
         const int nc = gamg_agglomerate(F, w, F.agg);
         if (nc >= F.n) break;
-        // coarse faces: (min, max) aggregate pairs, sorted, fine faces in ascending order
-        std::vector<std::pair<long long, int>> keyed;
-        keyed.reserve(F.nf);
+        // coarse faces: (min, max) aggregate pairs, sorted, fine faces in
+        // ascending order within each pair: two stable counting-sort passes
+        // (by max, then by min) over the faces in face order, O(F + nc)
+        std::vector<int> fa, fb, ord, tmp;
+        fa.reserve(F.nf);
+        fb.reserve(F.nf);
         for (int f = 0; f < F.nf; f++) {
             const int a = F.agg[F.l[f]], b = F.agg[F.u[f]];
-            if (a != b) keyed.push_back({(long long)std::min(a, b) * nc + std::max(a, b), f});
+            if (a != b) {
+                fa.push_back(std::min(a, b));
+                fb.push_back(std::max(a, b));
+                ord.push_back(f);
+            }
         }
-        std::stable_sort(keyed.begin(), keyed.end(),
-                         [](const std::pair<long long, int>& x, const std::pair<long long, int>& y) {
-                             return x.first < y.first;
-                         });
+        const size_t m = ord.size();
+        {
+            std::vector<int> pos(nc + 1, 0);
+            std::vector<int> key(m);
+            tmp.resize(m);
+            for (int pass = 0; pass < 2; pass++) {   // pass 0: by max (fb), pass 1: by min (fa)
+                const std::vector<int>& k = pass == 0 ? fb : fa;
+                std::fill(pos.begin(), pos.end(), 0);
+                for (size_t j = 0; j < m; j++) {
+                    key[j] = k[pass == 0 ? j : (size_t)tmp[j]];
+                    pos[key[j] + 1]++;
+                }
+                for (int c = 0; c < nc; c++) pos[c + 1] += pos[c];
+                std::vector<int> out(m);
+                for (size_t j = 0; j < m; j++) out[pos[key[j]]++] = pass == 0 ? (int)j : tmp[j];
+                tmp.swap(out);
+            }
+        }
+        // tmp: indices into (fa, fb, ord) sorted by (min, max), ties in face order
         GamgHostLevel C;
         C.n = nc;
         F.fptr.assign(1, 0);
+        F.fface.reserve(m);
         std::vector<double> wc;
-        for (size_t j = 0; j < keyed.size(); j++) {
-            if (j == 0 || keyed[j].first != keyed[j - 1].first) {
+        for (size_t j = 0; j < m; j++) {
+            const int t = tmp[j];
+            if (j == 0 || fa[t] != fa[tmp[j - 1]] || fb[t] != fb[tmp[j - 1]]) {
                 if (j > 0) F.fptr.push_back((int)j);
-                C.l.push_back((int)(keyed[j].first / nc));
-                C.u.push_back((int)(keyed[j].first % nc));
+                C.l.push_back(fa[t]);
+                C.u.push_back(fb[t]);
                 wc.push_back(0.0);
             }
-            wc.back() += w[keyed[j].second];
-            F.fface.push_back(keyed[j].second);
+            wc.back() += w[ord[t]];
+            F.fface.push_back(ord[t]);
         }
-        F.fptr.push_back((int)keyed.size());
+        F.fptr.push_back((int)m);
         C.nf = (int)C.l.size();
         // next-level cell -> cells, -> faces inside it (ascending)
         F.cptr.assign(nc + 1, 0);
@@ -736,6 +878,14 @@ spuma_status spuma_gamg_bind(spuma_gamg_t g, void* workspace, size_t workspace_b
             SPUMA_CUDA(up(D.iface, H.iface));
         }
     }
+    if (g->agg_int && g->h->n > 0) {
+        spuma_ldu_t h = g->h;
+        k_gamg_lvl0_maps<<<std::min(4 * h->num_sms, (h->n + 255) / 256), 256, 0, s>>>(
+            h->n, h->at<int>(h->L.perm), h->at<int>(h->L.iperm), g->hlv[0].agg, g->hlv[0].ccell, g->agg_int,
+            g->ccell_int);
+        SPUMA_CUDA(cudaGetLastError());
+        count_launch();
+    }
     SPUMA_CUDA(cudaStreamSynchronize(s));
     return SPUMA_OK;
 }
@@ -788,6 +938,29 @@ spuma_status spuma_gamg_solve(spuma_gamg_t g, const double* diag, const double* 
     a.smoother = g->smoother;
     a.coarsest_precond = g->coarsest_precond;
     a.partials = g->partials;
+    if (g->agg_int) {
+        // level 0 in internal order; its coefficients overwrite the handle's
+        // matrix region, so the next PCG solve prepares its matrix again
+        GamgLvl0& z = a.z;
+        z.on = 1;
+        z.n = h->n;
+        z.ell_w = h->ell_w;
+        z.perm = h->at<int>(h->L.perm);
+        z.Lptr = h->at<int>(h->L.Lptr);
+        z.Lcol = h->at<int>(h->L.Lcol);
+        z.Lface = h->at<int>(h->L.Lface);
+        z.Uptr = h->at<int>(h->L.Uptr);
+        z.Ucol = h->at<int>(h->L.Ucol);
+        z.Uface = h->at<int>(h->L.Uface);
+        z.Ecol = h->at<int>(h->L.Ecol);
+        z.La = h->at<double>(h->L.La64);
+        z.Ua = h->at<double>(h->L.Ua64);
+        z.d = h->at<double>(h->L.d64);
+        z.Ea = h->at<double>(h->L.Ea64);
+        z.agg_int = g->agg_int;
+        z.ccell_int = g->ccell_int;
+        h->prepared_precond = -1;
+    }
     a.status = h->at<int>(h->L.status);
     a.perf = perf;
     a.max_iter = ctl->max_iter;

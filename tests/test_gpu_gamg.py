@@ -99,3 +99,23 @@ def test_options_rejected():
         GamgSolver(M, dev(np.linalg.norm(c.mesh.sf, axis=1)), smoother=2)
     with pytest.raises(SpumaError):
         GamgSolver(M, dev(np.linalg.norm(c.mesh.sf, axis=1)), coarsest_precond=0)
+
+
+def test_gamg_then_prepared_matrix_calls(gc):
+    """A multi-level GAMG solve gathers its level-0 coefficients into the mesh
+    handle's matrix region: a preconditioner prepared before is refused until
+    it is prepared again, and PCG solves on the same handle are unaffected."""
+    from paper_2512_22215_gb300 import SolverControls, SpumaError
+    c, m, M, S, w, up, dg = gc
+    r = dev(c.b)
+    M.prepare(dev(dg), dev(up), 2)
+    w0 = M.precondition(r, 2).cpu().numpy()
+    x0, p0 = M.solve(dev(dg), dev(up), dev(c.b), None, SolverControls(precond=2, tolerance=1e-10))
+    S.solve(dev(dg * 1.5), dev(up * 1.5), dev(c.b), None, SolverControls(tolerance=1e-8, max_iter=500))
+    if len(S.level_cells) >= 2:
+        with pytest.raises(SpumaError):
+            M.precondition(r, 2)
+    M.prepare(dev(dg), dev(up), 2)
+    assert np.array_equal(M.precondition(r, 2).cpu().numpy(), w0)
+    x1, p1 = M.solve(dev(dg), dev(up), dev(c.b), None, SolverControls(precond=2, tolerance=1e-10))
+    assert p1["n_iter"] == p0["n_iter"] and np.array_equal(x1.cpu().numpy(), x0.cpu().numpy())
