@@ -125,7 +125,7 @@ typedef struct {
  * into the workspace, which must stay allocated and untouched until
  * spuma_ldu_destroy().  The addressing arrays are copied; the caller may free
  * them after create returns.  flags: 0, or SPUMA_WORKSPACE_ASYMMETRIC for a
- * workspace that also holds what spuma_pbicg_solve needs (32F + 8N more
+ * workspace that also holds what spuma_pbicg_solve needs (48F + 16N more
  * bytes); create detects the larger size by itself.
  * ---------------------------------------------------------------------- */
 size_t spuma_workspace_bytes(int32_t n_cells, int32_t n_faces, int32_t flags);

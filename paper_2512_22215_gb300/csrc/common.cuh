@@ -287,6 +287,7 @@ struct Layout {
     // SPUMA_WORKSPACE_ASYMMETRIC: A^T's coefficients in the internal CSR, the
     // transposed DILU sweep coefficients, the transposed search direction
     size_t LaT64, UaT64, LcT64, UcT64, pT64;
+    size_t EaT64;  // A^T's coefficients in the fixed-width Amul layout (A's go to Ea64)
     bool asym = false;
 };
 

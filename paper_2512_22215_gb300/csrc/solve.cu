@@ -459,6 +459,24 @@ __device__ bool phase_gather(const SolveArgs& a, const Group& g)
             const double dv = a.diag_orig[a.perm[p]];
             a.d64[p] = dv;
             bad |= !isfinite(dv);
+            if (a.ell_w > 0) {
+                // fixed-width layout: A (lower_f in row u, upper_f in row l) and A^T
+                const int l0 = a.Lptr[p], nl = a.Lptr[p + 1] - l0, u0 = a.Uptr[p], nt = nl + a.Uptr[p + 1] - u0;
+                for (int j = 0; j < a.ell_w; j++) {
+                    double v = 0.0, vt = 0.0;
+                    if (j < nl) {
+                        const int f = a.Lface[l0 + j];
+                        v = a.lower_orig[f];
+                        vt = a.upper_orig[f];
+                    } else if (j < nt) {
+                        const int f = a.Uface[u0 + j - nl];
+                        v = a.upper_orig[f];
+                        vt = a.lower_orig[f];
+                    }
+                    a.Ea64[(size_t)j * a.n + p] = v;
+                    a.EaT64[(size_t)j * a.n + p] = vt;
+                }
+            }
         }
     } else {
         gather_symmetric(a, it, bad);
@@ -1195,6 +1213,7 @@ __device__ bool solve_pbicg(const SolveArgs& a, const Group& g, double nfac, dou
     AT.Ua = a.UaT64;
     AT.Lc = a.LcT64;
     AT.Uc = a.UcT64;
+    AT.Ea = a.EaT64;
     double *x = a.x, *rA = a.r, *wA = a.w, *pA = a.p, *wT = a.q, *rT = a.b, *pT = a.pT;
     PhaseClock pc(a.phase_clk, g.bid);
     for (int p = it.first; p < a.n; p += it.stride) rT[p] = a.b[p] - amul_row<double>(AT, x, p);
@@ -1529,6 +1548,7 @@ SolveArgs make_args(spuma_ldu_t h)
     a.LcT64 = L.asym ? h->at<double>(L.LcT64) : nullptr;
     a.UcT64 = L.asym ? h->at<double>(L.UcT64) : nullptr;
     a.pT = L.asym ? h->at<double>(L.pT64) : nullptr;
+    a.EaT64 = L.asym ? h->at<double>(L.EaT64) : nullptr;
     a.Ecol = h->at<int>(L.Ecol);
     a.Ea64 = h->at<double>(L.Ea64);
     a.Ea32 = h->at<float>(L.Ea32);
@@ -1809,7 +1829,6 @@ spuma_status spuma_pbicg_solve(spuma_ldu_t h, const double* diag, const double* 
     a.b_orig = b;
     a.x_orig = x;
     a.perf = perf;
-    a.ell_w = 0;   // the fixed-width layout holds no asymmetric coefficients: row-extent Amul/Tmul
     h->prepared_precond = -1;
     return launch_solve(h, a, default_threads(ctl), s);
 }

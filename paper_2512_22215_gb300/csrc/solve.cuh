@@ -30,6 +30,7 @@ struct SolveArgs {
     double *La64, *Ua64, *Lc64, *Uc64, *d64, *rD64;
     float *La32, *Ua32, *Lc32, *Uc32, *d32, *rD32;
     double *LaT64, *UaT64, *LcT64, *UcT64, *pT;  // asymmetric regions (NULL without them)
+    double* EaT64;         // asymmetric: A^T in the fixed-width layout (A in Ea64)
     const int* Ecol;       // fixed-width Amul layout (ell_w > 0): columns, entry j of row p at j n + p
     double* Ea64;
     float* Ea32;

@@ -102,6 +102,7 @@ Layout make_layout(int64_t n, int64_t nf, bool asym)
         L.LcT64 = take(d8f);
         L.UcT64 = take(d8f);
         L.pT64 = take(d8n);
+        L.EaT64 = take(8 * L.ell_slots);
     }
     L.bytes = off;
     return L;

@@ -191,4 +191,4 @@ def test_asymmetric_workspace_is_larger(L):
     n, f = 1000, 2700
     sym = L.spuma_workspace_bytes(n, f, 0)
     asym = L.spuma_workspace_bytes(n, f, 1)
-    assert asym >= sym + 32 * f + 8 * n
+    assert asym >= sym + 48 * f + 16 * n
