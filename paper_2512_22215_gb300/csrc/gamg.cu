@@ -43,10 +43,12 @@ constexpr int kGamgPostSweeps = 2;
 constexpr double kGamgCoarseRelTol = 1e-8;
 enum GamgSlot { GS_A = 0, GS_B = 1, GS_C = 2, GS_D = 3 };   // reduction slots
 
-// Device view of one level (rows in the original order of that level).
+// Device view of one level (rows in the level's storage order: see
+// gamg_store_order; faces in the level's own numbering).
 struct GamgLevel {
     int n, nf;
     const int *rptr, *rcol, *rfac;          // row CSR for A_k: entries in ascending face order
+    const int* rlo;                         // lower entries of each row (leading its entries)
     const int* agg;                         // cell -> next-level cell (k < L-1)
     const int *cptr, *ccell;                // next-level cell -> its cells (ascending)
     const int *fptr, *fface;                // next-level face -> its faces (ascending)
@@ -62,14 +64,15 @@ struct GamgLevel {
 // Morton order inside a level): the solver's internal CSR (lower entries,
 // then upper, each in face order) and, when the mesh has it, its fixed-width
 // Amul layout, their coefficients gathered from the caller's arrays at the
-// start of each solve; the aggregation lists mapped to internal positions at
-// bind.  Every row sum keeps its face order, so the results are those of the
-// original-order level.  Used when the hierarchy has more than one level.
+// start of each solve; the aggregation lists at internal positions (built
+// with the hierarchy).  Every row sum keeps its face order, so the results
+// are those of the original-order level.  Used when the hierarchy has more
+// than one level.
 struct GamgLvl0 {
     int on, n, ell_w;
     const int *perm, *Lptr, *Lcol, *Lface, *Uptr, *Ucol, *Uface, *Ecol;
     double *La, *Ua, *d, *Ea;             // the handle's matrix region, filled per solve
-    const int *agg_int, *ccell_int;       // agg[perm[p]], iperm[ccell[j]]
+    const int* ccell_int;                 // level 0's aggregate lists at internal positions
 };
 
 struct GamgArgs {
@@ -88,9 +91,31 @@ struct GamgArgs {
     spuma_solver_perf* perf;
     int max_iter, min_iter;
     double tol, rel_tol;
+    long long* clk;                         // optional per-phase SM-clock totals of block 0 (diagnostics)
 };
 
 // --------------------------------------------------------------- device ---
+// Optional phase timing (SPUMA_PHASE_CLOCKS): block 0's thread 0 adds SM-clock
+// deltas into clk[slot]: 0..49 restriction into level k+1 (slot k), 64..113
+// prolongation, scaling and smoothing of level k (64 + k), 128 the coarsest
+// level, 129 the outer update and residual, 130 V-cycles counted.
+struct GamgClock {
+    long long* acc;
+    long long t;
+    __device__ __forceinline__ GamgClock(long long* a, int bid)
+    {
+        acc = (a && bid == 0 && threadIdx.x == 0) ? a : nullptr;
+        t = clock64();
+    }
+    __device__ __forceinline__ void lap(int slot)
+    {
+        if (acc) {
+            const long long now = clock64();
+            acc[slot] += now - t;
+            t = now;
+        }
+    }
+};
 struct Exec {
     int first, stride;
     bool grid, active;
@@ -124,18 +149,45 @@ __device__ __forceinline__ bool exec_sum(const Exec& x, double (&v)[NV], const G
         return true;
     }
     if (g.bid != 0) return true;
-    block_reduce_store<NV>(v, a.partials, slot, 0);
+    // the first block alone: the same sums through shared memory only
+    __shared__ double red[NV][32];
+    __shared__ double bc[NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double s = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        v[k] = s;
+    }
     __syncthreads();
-    grid_reduce_read<NV>(v, a.partials, slot, 1);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; k++) red[k][warp] = v[k];
+    __syncthreads();
+    if (warp == 0)
+#pragma unroll
+        for (int k = 0; k < NV; k++) {
+            double s = lane < nw ? red[k][lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) bc[k] = s;
+        }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = bc[k];
+    __syncthreads();
     return true;
 }
 
 // (A_k x)_i: d_i x_i, then the row's entries in face order, one FMA each;
 // entries loaded in groups of 8 (columns and coefficients, then the
 // gathers), the FMAs in entry order.
-__device__ __forceinline__ double gamg_amul_row(const GamgLevel& L, const double* d, const double* x, int i)
+// X(c) gives x_c (a plain load, or a gather through the aggregation map).
+template <class X>
+__device__ __forceinline__ double gamg_amul_row_g(const GamgLevel& L, const double* d, X x, int i)
 {
-    double y = __dmul_rn(d[i], x[i]);
+    double y = __dmul_rn(d[i], x(i));
     const int e1 = L.rptr[i + 1];
     for (int e0 = L.rptr[i]; e0 < e1; e0 += 8) {
         int c[8];
@@ -147,20 +199,25 @@ __device__ __forceinline__ double gamg_amul_row(const GamgLevel& L, const double
             v[j] = ok ? L.rval[e0 + j] : 0.0;
         }
 #pragma unroll
-        for (int j = 0; j < 8; j++) xv[j] = c[j] >= 0 ? x[c[j]] : 0.0;
+        for (int j = 0; j < 8; j++) xv[j] = c[j] >= 0 ? x(c[j]) : 0.0;
 #pragma unroll
         for (int j = 0; j < 8; j++)
             if (c[j] >= 0) y = __fma_rn(v[j], xv[j], y);
     }
     return y;
 }
+__device__ __forceinline__ double gamg_amul_row(const GamgLevel& L, const double* d, const double* x, int i)
+{
+    return gamg_amul_row_g(L, d, [x](int c) { return x[c]; }, i);
+}
 
 // (A_0 x)_p in internal order: d_p x_p, then the row's entries in face order
 // (fixed-width layout, or lower then upper CSR entries), one FMA each; entry
 // loads grouped, then the gathers, then the FMAs in order.
-__device__ __forceinline__ double lvl0_amul_row(const GamgLvl0& z, const double* x, int p)
+template <class X>
+__device__ __forceinline__ double lvl0_amul_row(const GamgLvl0& z, X x, int p)
 {
-    double y = __dmul_rn(z.d[p], x[p]);
+    double y = __dmul_rn(z.d[p], x(p));
     if (z.ell_w > 0) {
         for (int j0 = 0; j0 < z.ell_w; j0 += 6) {
             int c[6];
@@ -173,23 +230,24 @@ __device__ __forceinline__ double lvl0_amul_row(const GamgLvl0& z, const double*
                 v[j] = ok ? __ldcs(z.Ea + e) : 0.0;
             }
 #pragma unroll
-            for (int j = 0; j < 6; j++) xv[j] = c[j] >= 0 ? x[c[j]] : 0.0;
+            for (int j = 0; j < 6; j++) xv[j] = c[j] >= 0 ? x(c[j]) : 0.0;
 #pragma unroll
             for (int j = 0; j < 6; j++)
                 if (c[j] >= 0) y = __fma_rn(v[j], xv[j], y);
         }
         return y;
     }
-    for (int e = z.Lptr[p]; e < z.Lptr[p + 1]; e++) y = __fma_rn(z.La[e], x[z.Lcol[e]], y);
-    for (int e = z.Uptr[p]; e < z.Uptr[p + 1]; e++) y = __fma_rn(z.Ua[e], x[z.Ucol[e]], y);
+    for (int e = z.Lptr[p]; e < z.Lptr[p + 1]; e++) y = __fma_rn(z.La[e], x(z.Lcol[e]), y);
+    for (int e = z.Uptr[p]; e < z.Uptr[p + 1]; e++) y = __fma_rn(z.Ua[e], x(z.Ucol[e]), y);
     return y;
 }
 
 // A level's row operations, in internal order at level 0 when z.on.
 __device__ __forceinline__ double level_amul_row(const GamgArgs& a, int k, const double* x, int i)
 {
-    if (k == 0 && a.z.on) return lvl0_amul_row(a.z, x, i);
-    return gamg_amul_row(a.lv[k], a.lv[k].diag, x, i);
+    auto xv = [x](int c) { return x[c]; };
+    if (k == 0 && a.z.on) return lvl0_amul_row(a.z, xv, i);
+    return gamg_amul_row_g(a.lv[k], a.lv[k].diag, xv, i);
 }
 
 // s - sum over the row's lower entries (face order) of a_f y_col, one FMA each
@@ -201,10 +259,8 @@ __device__ __forceinline__ double level_lower_sweep(const GamgArgs& a, int k, co
         return s;
     }
     const GamgLevel& L = a.lv[k];
-    for (int e = L.rptr[i]; e < L.rptr[i + 1]; e++) {
-        const int c = L.rcol[e];
-        if (c < i) s = __fma_rn(-L.rval[e], y[c], s);
-    }
+    const int e0 = L.rptr[i], e1 = e0 + L.rlo[i];
+    for (int e = e0; e < e1; e++) s = __fma_rn(-L.rval[e], y[L.rcol[e]], s);
     return s;
 }
 
@@ -379,8 +435,9 @@ __device__ bool gamg_coarsest(const GamgArgs& a, const Group& g)
     return exec_sync(x, g);
 }
 
-// e_0 = V(0, r_0), with r_0 = a.res.
-__device__ bool gamg_vcycle(const GamgArgs& a, const Group& g)
+// e_0 = V(0, r_0), with r_0 = a.res; the last smoothing sweep of level 0 also
+// adds e_0 to x (the outer update, fused).
+__device__ bool gamg_vcycle(const GamgArgs& a, const Group& g, GamgClock& ck)
 {
     // restriction down to the coarsest level
     for (int k = 0; k + 1 < a.nlev; k++) {
@@ -395,17 +452,18 @@ __device__ bool gamg_vcycle(const GamgArgs& a, const Group& g)
                 C.r[c] = s;
             }
         if (!exec_sync(x, g)) return false;
+        ck.lap(k);
     }
     if (!gamg_coarsest(a, g)) return false;
+    ck.lap(128);
     // prolongation, scaling and smoothing back up
     for (int k = a.nlev - 2; k >= 0; k--) {
         const GamgLevel& L = a.lv[k];
         const GamgLevel& C = a.lv[k + 1];
         if (k + 1 == a.small_from && !group_sync(g)) return false;   // the first block's levels are done
         const Exec x = exec_for(a, k, g);
-        const int* ag = k == 0 && a.z.on ? a.z.agg_int : L.agg;
         if (x.active)
-            for (int i = x.first; i < L.n; i += x.stride) L.e[i] = C.e[ag[i]];
+            for (int i = x.first; i < L.n; i += x.stride) L.e[i] = C.e[L.agg[i]];
         if (!exec_sync(x, g)) return false;
         double v[2] = {0.0, 0.0};
         if (x.active)
@@ -432,10 +490,13 @@ __device__ bool gamg_vcycle(const GamgArgs& a, const Group& g)
                         L.y[i] = __dmul_rn(L.wrd[i], qi);
                     }
                 if (!exec_sync(x, g)) return false;
+                const bool fold = k == 0 && s == kGamgPostSweeps - 1;   // x += e_0 here
                 if (x.active)
                     for (int i = x.first; i < L.n; i += x.stride) {
                         const double si = level_lower_sweep(a, k, L.y, i, L.q[i]);
-                        L.e[i] = __dadd_rn(L.e[i], __dmul_rn(L.wrd[i], si));
+                        const double ei = __dadd_rn(L.e[i], __dmul_rn(L.wrd[i], si));
+                        L.e[i] = ei;
+                        if (fold) a.x[i] = __dadd_rn(a.x[i], ei);
                     }
                 if (!exec_sync(x, g)) return false;
             }
@@ -445,12 +506,17 @@ __device__ bool gamg_vcycle(const GamgArgs& a, const Group& g)
             for (int s = 0; s < kGamgPostSweeps; s++) {
                 const double* src = (s & 1) ? L.q : L.e;
                 double* dst = (s & 1) ? L.e : L.q;
+                const bool fold = k == 0 && s == kGamgPostSweeps - 1;   // x += e_0 here
                 if (x.active)
-                    for (int i = x.first; i < L.n; i += x.stride)
-                        dst[i] = __fma_rn(L.wrd[i], __dsub_rn(L.r[i], level_amul_row(a, k, src, i)), src[i]);
+                    for (int i = x.first; i < L.n; i += x.stride) {
+                        const double ei = __fma_rn(L.wrd[i], __dsub_rn(L.r[i], level_amul_row(a, k, src, i)), src[i]);
+                        dst[i] = ei;
+                        if (fold) a.x[i] = __dadd_rn(a.x[i], ei);
+                    }
                 if (!exec_sync(x, g)) return false;
             }
         }
+        ck.lap(64 + k);
     }
     if (a.nlev == 1 || a.small_from == 0) return group_sync(g);
     return true;
@@ -514,14 +580,17 @@ __global__ void __launch_bounds__(1024, 1) k_gamg(GamgArgs a, unsigned long long
     }
     auto conv = [&](double rr) { return rr < a.tol || (a.rel_tol > 0.0 && rr < a.rel_tol * res0); };
     int n_it = 0;
+    GamgClock ck(a.clk, g.bid);
     if (ok && (a.min_iter > 0 || !conv(res0))) {
         for (;;) {
-            ok = gamg_vcycle(a, g);
+            ok = gamg_vcycle(a, g, ck);
             if (!ok) break;
             double acc[1] = {0.0};
-            for (int i = it.first; i < L0.n; i += it.stride) a.x[i] = __dadd_rn(a.x[i], L0.e[i]);
-            ok = group_sync(g);
-            if (!ok) break;
+            if (a.nlev == 1) {   // otherwise the last smoothing sweep of level 0 added e_0 to x
+                for (int i = it.first; i < L0.n; i += it.stride) a.x[i] = __dadd_rn(a.x[i], L0.e[i]);
+                ok = group_sync(g);
+                if (!ok) break;
+            }
             for (int i = it.first; i < L0.n; i += it.stride) {
                 const double r = a.b[i] - level_amul_row(a, 0, a.x, i);
                 a.res[i] = r;
@@ -533,6 +602,8 @@ __global__ void __launch_bounds__(1024, 1) k_gamg(GamgArgs a, unsigned long long
             grid_reduce_read<1>(acc, a.partials, GS_C, g.nblocks);
             res = acc[0] / nfac;
             n_it++;
+            ck.lap(129);
+            if (ck.acc) ck.acc[130] += 1;
             if (!((n_it < a.max_iter && !conv(res)) || n_it < a.min_iter)) break;
         }
     }
@@ -567,24 +638,14 @@ __global__ void __launch_bounds__(1024, 1) k_gamg(GamgArgs a, unsigned long long
     }
 }
 
-// Level 0's aggregation lists at internal positions: agg_int[p] = agg[perm[p]],
-// ccell_int[j] = iperm[ccell[j]].
-__global__ void k_gamg_lvl0_maps(int n, const int* __restrict__ perm, const int* __restrict__ iperm,
-                                 const int* __restrict__ agg, const int* __restrict__ ccell, int* agg_int,
-                                 int* ccell_int)
-{
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        agg_int[p] = agg[perm[p]];
-        ccell_int[p] = iperm[ccell[p]];
-    }
-}
-
 // ----------------------------------------------------------------- host ---
 struct GamgHostLevel {
     int n = 0, nf = 0;
     std::vector<int> l, u;                   // faces of this level (sorted by (l, u))
     std::vector<int> rptr, rcol, rfac;       // row CSR
+    std::vector<int> rlo;                    // lower entries of each row (they come first)
     std::vector<int> agg, cptr, ccell, fptr, fface, iptr, iface;   // towards the next level
+    std::vector<int> ccell_int;              // level 0: ccell at internal positions
 };
 
 static void gamg_rows(GamgHostLevel& L)
@@ -604,6 +665,93 @@ static void gamg_rows(GamgHostLevel& L)
         L.rfac[cur[a]++] = f;
         L.rcol[cur[b]] = a;
         L.rfac[cur[b]++] = f;
+    }
+}
+
+// Storage order of the levels; the results do not change.  Level 0 is kept
+// in the mesh handle's internal order (when there are coarse levels), level
+// k in the order of each aggregate's first member in level k-1's storage
+// order (so the coarse levels inherit level 0's Morton locality), and the
+// coarsest level in its own order.  Rows, aggregates and their lists are
+// moved, never reordered inside: a row keeps its entries in face order, an
+// aggregate its cells in ascending original order, so every sum is taken
+// in the same order.  Afterwards: rows (rptr, rcol, rfac, rlo) of levels >= 1
+// in storage order with columns at storage positions; agg maps storage
+// positions to the next level's; cptr/ccell and iptr/iface follow the next
+// level's storage order, with ccell at storage positions (level 0: original
+// cell numbers, which index the caller's diagonal, and ccell_int at internal
+// positions); faces (fptr, fface, l, u) keep their numbering.  perm0:
+// internal position -> original cell of level 0.
+static void gamg_store_order(std::vector<GamgHostLevel>& lv, const std::vector<int>& perm0)
+{
+    const int L = (int)lv.size();
+    std::vector<std::vector<int>> pos(L), inv(L);
+    for (int k = 0; k < L; k++) {
+        const int n = lv[k].n;
+        pos[k].assign(n, -1);
+        inv[k].assign(n, 0);
+        if (k == L - 1) {
+            for (int i = 0; i < n; i++) pos[k][i] = inv[k][i] = i;
+        } else if (k == 0) {
+            for (int p = 0; p < n; p++) {
+                inv[0][p] = perm0[p];
+                pos[0][perm0[p]] = p;
+            }
+        } else {
+            int next = 0;
+            for (int q = 0; q < lv[k - 1].n; q++) {
+                const int c = lv[k - 1].agg[inv[k - 1][q]];
+                if (pos[k][c] < 0) {
+                    pos[k][c] = next;
+                    inv[k][next++] = c;
+                }
+            }
+        }
+    }
+    for (int k = 0; k < L; k++) {
+        GamgHostLevel& H = lv[k];
+        // rows: lower entries (column below the row in the original order)
+        // lead each row, faces being sorted by (lower, upper)
+        std::vector<int> rptr(H.n + 1, 0), rcol, rfac, rlo(H.n, 0);
+        rcol.reserve(H.rcol.size());
+        rfac.reserve(H.rfac.size());
+        for (int q = 0; q < H.n; q++) {
+            const int c = k == 0 ? q : inv[k][q];   // level 0's rows stay in original order
+            const int* P = k == 0 ? nullptr : pos[k].data();
+            for (int e = H.rptr[c]; e < H.rptr[c + 1]; e++) {
+                rcol.push_back(P ? P[H.rcol[e]] : H.rcol[e]);
+                rfac.push_back(H.rfac[e]);
+                if (H.rcol[e] < c) rlo[q]++;
+            }
+            rptr[q + 1] = (int)rcol.size();
+        }
+        H.rptr.swap(rptr);
+        H.rcol.swap(rcol);
+        H.rfac.swap(rfac);
+        H.rlo.swap(rlo);
+        if (k + 1 >= L) continue;
+        const int nc = lv[k + 1].n;
+        std::vector<int> agg(H.n), cptr(nc + 1, 0), ccell, iptr(nc + 1, 0), iface, ccell_int;
+        for (int q = 0; q < H.n; q++) agg[q] = pos[k + 1][H.agg[inv[k][q]]];
+        ccell.reserve(H.ccell.size());
+        iface.reserve(H.iface.size());
+        for (int qc = 0; qc < nc; qc++) {
+            const int c = inv[k + 1][qc];
+            for (int j = H.cptr[c]; j < H.cptr[c + 1]; j++) {
+                const int fine = H.ccell[j];
+                ccell.push_back(k == 0 ? fine : pos[k][fine]);
+                if (k == 0) ccell_int.push_back(pos[0][fine]);
+            }
+            for (int j = H.iptr[c]; j < H.iptr[c + 1]; j++) iface.push_back(H.iface[j]);
+            cptr[qc + 1] = (int)ccell.size();
+            iptr[qc + 1] = (int)iface.size();
+        }
+        H.agg.swap(agg);
+        H.cptr.swap(cptr);
+        H.ccell.swap(ccell);
+        H.iptr.swap(iptr);
+        H.iface.swap(iface);
+        H.ccell_int.swap(ccell_int);
     }
 }
 
@@ -654,7 +802,7 @@ struct spuma_gamg {
     double *x = nullptr, *b = nullptr, *pw = nullptr, *pp = nullptr, *pq = nullptr, *px = nullptr;
     double* crD = nullptr;
     double* partials = nullptr;
-    int *agg_int = nullptr, *ccell_int = nullptr;   // level 0 in internal order (two or more levels)
+    int* ccell_int = nullptr;              // level 0's aggregate lists at internal positions (two or more levels)
     int small_from = 0;
     int smoother = 0;                      // 0 Richardson, 1 two-stage Gauss-Seidel
     int coarsest_precond = SPUMA_PRECOND_DIAGONAL;
@@ -681,6 +829,7 @@ size_t gamg_layout(spuma_gamg& G, bool assign)
         D.rptr = (int*)take(4 * H.rptr.size());
         D.rcol = (int*)take(4 * H.rcol.size() + 4);
         D.rfac = (int*)take(4 * H.rfac.size() + 4);
+        D.rlo = (int*)take(4 * H.rlo.size() + 4);
         if (k + 1 < L) {
             D.agg = (int*)take(4 * H.agg.size() + 4);
             D.cptr = (int*)take(4 * H.cptr.size());
@@ -714,11 +863,7 @@ size_t gamg_layout(spuma_gamg& G, bool assign)
     G.px = (double*)take(8 * nc + 8);
     G.crD = (double*)take(8 * nc + 8);
     G.partials = (double*)take(8 * (size_t)kMaxBlocks * kSlots);
-    G.agg_int = G.ccell_int = nullptr;
-    if (L >= 2) {
-        G.agg_int = (int*)take(4 * n0 + 4);
-        G.ccell_int = (int*)take(4 * n0 + 4);
-    }
+    G.ccell_int = L >= 2 ? (int*)take(4 * n0 + 4) : nullptr;
     return off;
 }
 
@@ -832,6 +977,17 @@ spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_s
         G->lv.push_back(std::move(C));
         w.swap(wc);
     }
+    std::vector<int> perm0;
+    if (G->lv.size() >= 2) {
+        perm0.resize(h->n);
+        e = cudaMemcpyAsync(perm0.data(), h->at<int>(h->L.perm), 4 * (size_t)h->n, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            delete G;
+            return cuda_fail(e, "spuma_gamg_create: copy of the cell order");
+        }
+    }
+    gamg_store_order(G->lv, perm0);
     G->bytes = gamg_layout(*G, false);
     G->small_from = (int)G->lv.size();
     for (int k = 0; k < (int)G->lv.size(); k++)
@@ -868,6 +1024,7 @@ spuma_status spuma_gamg_bind(spuma_gamg_t g, void* workspace, size_t workspace_b
         SPUMA_CUDA(up(D.rptr, H.rptr));
         SPUMA_CUDA(up(D.rcol, H.rcol));
         SPUMA_CUDA(up(D.rfac, H.rfac));
+        SPUMA_CUDA(up(D.rlo, H.rlo));
         if (k + 1 < g->lv.size()) {
             SPUMA_CUDA(up(D.agg, H.agg));
             SPUMA_CUDA(up(D.cptr, H.cptr));
@@ -878,14 +1035,7 @@ spuma_status spuma_gamg_bind(spuma_gamg_t g, void* workspace, size_t workspace_b
             SPUMA_CUDA(up(D.iface, H.iface));
         }
     }
-    if (g->agg_int && g->h->n > 0) {
-        spuma_ldu_t h = g->h;
-        k_gamg_lvl0_maps<<<std::min(4 * h->num_sms, (h->n + 255) / 256), 256, 0, s>>>(
-            h->n, h->at<int>(h->L.perm), h->at<int>(h->L.iperm), g->hlv[0].agg, g->hlv[0].ccell, g->agg_int,
-            g->ccell_int);
-        SPUMA_CUDA(cudaGetLastError());
-        count_launch();
-    }
+    if (g->ccell_int) SPUMA_CUDA(up(g->ccell_int, g->lv[0].ccell_int));
     SPUMA_CUDA(cudaStreamSynchronize(s));
     return SPUMA_OK;
 }
@@ -938,7 +1088,7 @@ spuma_status spuma_gamg_solve(spuma_gamg_t g, const double* diag, const double* 
     a.smoother = g->smoother;
     a.coarsest_precond = g->coarsest_precond;
     a.partials = g->partials;
-    if (g->agg_int) {
+    if (g->ccell_int) {
         // level 0 in internal order; its coefficients overwrite the handle's
         // matrix region, so the next PCG solve prepares its matrix again
         GamgLvl0& z = a.z;
@@ -957,11 +1107,15 @@ spuma_status spuma_gamg_solve(spuma_gamg_t g, const double* diag, const double* 
         z.Ua = h->at<double>(h->L.Ua64);
         z.d = h->at<double>(h->L.d64);
         z.Ea = h->at<double>(h->L.Ea64);
-        z.agg_int = g->agg_int;
         z.ccell_int = g->ccell_int;
         h->prepared_precond = -1;
     }
     a.status = h->at<int>(h->L.status);
+    a.clk = nullptr;
+    if (getenv("SPUMA_PHASE_CLOCKS")) {
+        a.clk = h->at<long long>(h->L.clk);
+        SPUMA_CUDA(cudaMemsetAsync(a.clk, 0, 8 * 256, s));
+    }
     a.perf = perf;
     a.max_iter = ctl->max_iter;
     a.min_iter = ctl->min_iter;
