@@ -92,3 +92,18 @@ def test_mixed_reliable(wc):
     assert p["converged"] == 1 and p["status"] == 0 and p["n_outer"] >= 1
     r = b - oracle.amul(lo, ua, d, up, x.cpu().numpy())
     assert np.abs(r).sum() / np.abs(b).sum() < 1e-10
+
+
+def test_gamg_matched_iterations(wc):
+    """GAMG whose level 0 runs in internal order on the row-extent (CSR)
+    layout, against the oracle at matched V-cycles."""
+    from oracle import gamg as G
+    from paper_2512_22215_gb300 import GamgSolver, SolverControls
+    lo, ua, up, d, b, M = wc
+    w = np.abs(up)
+    S = GamgSolver(M, dev(w), smoother=1)
+    assert len(S.level_cells) >= 2
+    x, p = S.solve(dev(d), dev(up), dev(b), None, SolverControls(tolerance=1e-10, max_iter=500))
+    assert p["converged"] == 1 and p["status"] == 0
+    xo, _, _ = G.gamg(lo, ua, d, up, b, w, tol=0.0, max_iter=p["n_iter"], smoother="gs2")
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo)
