@@ -33,8 +33,8 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # bench workload by the per-iteration byte model (traffic grows with the
 # algorithmic bytes).  Valid only for the solver source it was taken with
 # (checked by hash, else the line reports null).
-TRAFFIC = {"solve_cu_sha1": "383f3b8816a30bba63c822218f49b9afb35ba7b5", "n": 128,
-           "bytes": 124951129344 + 2493560832, "inner": 524, "outer": 4}
+TRAFFIC = {"solve_cu_sha1": "b6798d6b171cc9be79cdaa9c0490dba6469f33d1", "n": 128,
+           "bytes": 124937681920 + 2498494208, "inner": 524, "outer": 4}
 # Iteration counts of this seeded workload (mixed: inner iterations, outer
 # steps), used only to project the CPU oracle's bounded sample to a full solve.
 PROJECTION_ITERS = {"inner": 795, "outer": 5}
