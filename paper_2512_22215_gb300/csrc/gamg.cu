@@ -414,6 +414,72 @@ __device__ void gamg_dic_seq(const GamgLevel& L, const double* rD, const double*
     }
 }
 
+// Sum over the warp's lanes (a butterfly: every lane gets the same value,
+// the same sum as the first block's reduction when only warp 0 holds values).
+__device__ __forceinline__ double warp_sum(double s)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// The coarsest level's PCG on warp 0 of the first block, one row per lane
+// (levels of at most 32 cells, the usual case): the same steps and sums as
+// gamg_coarsest below, with warp barriers instead of block barriers.
+__device__ void gamg_coarsest_warp(const GamgArgs& a, const GamgLevel& L)
+{
+    const int i = (int)threadIdx.x;
+    const bool row = i < L.n;
+    double* e = L.e;
+    double* r = a.pw;
+    double *w = a.pq, *p = a.pp, *q = a.px;
+    double ri = row ? L.r[i] : 0.0;
+    if (row) {
+        e[i] = 0.0;
+        r[i] = ri;
+    }
+    const double v0 = warp_sum(row ? fabs(ri) : 0.0);
+    const double nfac = v0 + 1e-20;
+    const double res0 = v0 / nfac;
+    double res = res0, rho = 1.0, rho_old;
+    const int max_it = 2 * L.n + 10;
+    int it = 0;
+    if (res0 > 0.0) {
+        do {
+            rho_old = rho;
+            double wi = 0.0;
+            if (a.coarsest_precond == SPUMA_PRECOND_DIC) {
+                __syncwarp();
+                if (i == 0) gamg_dic_seq(L, a.crD, r, w);
+                __syncwarp();
+                if (row) wi = w[i];
+            } else if (row) {
+                wi = __dmul_rn(__ddiv_rn(1.0, L.diag[i]), ri);
+                w[i] = wi;
+            }
+            rho = warp_sum(row ? __fma_rn(wi, ri, 0.0) : 0.0);
+            const double beta = it == 0 ? 0.0 : rho / rho_old;
+            if (row) p[i] = it == 0 ? wi : __fma_rn(beta, p[i], wi);
+            __syncwarp();
+            double qi = 0.0;
+            if (row) {
+                qi = gamg_amul_row(L, L.diag, p, i);
+                q[i] = qi;
+            }
+            const double s = warp_sum(row ? __fma_rn(qi, p[i], 0.0) : 0.0);
+            if (fabs(s) / nfac < 1e-300) break;
+            const double alpha = rho / s;
+            if (row) {
+                e[i] = __fma_rn(alpha, p[i], e[i]);
+                ri = __fma_rn(-alpha, qi, ri);
+                r[i] = ri;
+            }
+            res = warp_sum(row ? fabs(ri) : 0.0) / nfac;
+            __syncwarp();
+        } while (++it < max_it && !(res < kGamgCoarseRelTol * res0));
+    }
+}
+
 // Coarsest level: PCG with the diagonal preconditioner from 0, relative
 // tolerance kGamgCoarseRelTol, at most 2n + 10 iterations (PCG recurrences).
 __device__ bool gamg_coarsest(const GamgArgs& a, const Group& g)
@@ -422,6 +488,10 @@ __device__ bool gamg_coarsest(const GamgArgs& a, const Group& g)
     const GamgLevel& L = a.lv[k];
     const Exec x = exec_for(a, k, g);
     if (!x.active) return true;   // the coarsest level is the first block's alone
+    if (!x.grid && L.n <= 32) {
+        if (threadIdx.x < 32) gamg_coarsest_warp(a, L);
+        return exec_sync(x, g);
+    }
     double* e = L.e;
     double* r = a.pw;   // residual
     double *w = a.pq, *p = a.pp, *q = a.px;
