@@ -511,8 +511,14 @@ int32_t spuma_tune_cache_store(const char* path, const char* signature, int32_t 
  * SPUMA_TAIL_ROWS sets the row limit of the small last DIC levels that the
  * first block sweeps alone (0: none), SPUMA_SWEEP=0 strides a level's
  * rows over the blocks instead of giving each block one contiguous chunk of
- * every level, and SPUMA_AMUL_CHUNKS=1 makes the PCG's Amul phase walk those
- * chunks too (on meshes whose levels are wide).                            */
+ * every level, SPUMA_AMUL_CHUNKS=1 makes the PCG's Amul phase walk those
+ * chunks too (on meshes whose levels are wide), and
+ * SPUMA_GAMG_FUSE_SCALE_ROWS=n makes GAMG's coarse levels of at most n
+ * cells apply the correction's scaling inside their first smoothing sweep
+ * (0, the default: a pass of its own).  With SPUMA_PHASE_CLOCKS a GAMG
+ * solve fills the same table per V-cycle: 0..49 restriction into level
+ * k+1, 64..113 prolongation, scaling and smoothing of level k, 128 the
+ * coarsest level, 129 the outer update and residual, 130 V-cycles.        */
 spuma_status spuma_read_phase_clocks(spuma_ldu_t h, int64_t* out, int32_t n, spuma_stream_t stream);
 const char* spuma_status_string(int32_t status);
 const char* spuma_last_error(void);

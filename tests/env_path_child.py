@@ -1,5 +1,5 @@
-"""Child process of test_gpu_env_paths.py: runs the bit-exact DIC checks and
-the FP64 / mixed solves on one seeded case under whatever SPUMA_* variables
+"""Child process of test_gpu_env_paths.py: runs the bit-exact DIC checks, the
+FP64 / mixed solves and GAMG on one seeded case under whatever SPUMA_* variables
 the parent set (the library reads them once per process), and prints one
 JSON line with the comparisons against the oracle."""
 import json
@@ -39,6 +39,15 @@ def main():
     res = c.b - oracle.amul(m.lower, m.upper_addr, do, uo, x.cpu().numpy())
     out["mixed"] = {"converged": p["converged"], "status": p["status"],
                     "oracle_residual": float(np.abs(res).sum() / np.abs(c.b).sum())}
+    from oracle import gamg as G
+    from paper_2512_22215_gb300 import GamgSolver
+    wts = np.abs(uo)
+    for smoother, name in ((0, "richardson"), (1, "gs2")):
+        S = GamgSolver(M, dev(wts), smoother=smoother)
+        x, p = S.solve(dev(do), dev(uo), dev(c.b), None, SolverControls(tolerance=1e-10, max_iter=500))
+        xo, _, _ = G.gamg(m.lower, m.upper_addr, do, uo, c.b, wts, tol=0.0, max_iter=p["n_iter"], smoother=name)
+        out[f"gamg_{name}"] = {"converged": p["converged"], "status": p["status"], "levels": len(S.level_cells),
+                               "rel_err": float(np.linalg.norm(x.cpu().numpy() - xo) / np.linalg.norm(xo))}
     print(json.dumps(out), flush=True)
 
 
