@@ -515,7 +515,9 @@ int32_t spuma_tune_cache_store(const char* path, const char* signature, int32_t 
  * chunks too (on meshes whose levels are wide), and
  * SPUMA_GAMG_FUSE_SCALE_ROWS=n makes GAMG's coarse levels of at most n
  * cells apply the correction's scaling inside their first smoothing sweep
- * (0, the default: a pass of its own).  With SPUMA_PHASE_CLOCKS a GAMG
+ * (0, the default: a pass of its own); SPUMA_GAMG_ORDER=inherited (read by
+ * spuma_gamg_create) stores GAMG's middle levels in the order inherited
+ * from the level above instead of breadth-first.  With SPUMA_PHASE_CLOCKS a GAMG
  * solve fills the same table per V-cycle: 0..49 restriction into level
  * k+1, 64..113 prolongation, scaling and smoothing of level k, 128 the
  * coarsest level, 129 the outer update and residual, 130 V-cycles.        */

@@ -814,10 +814,10 @@ static void gamg_rows(GamgHostLevel& L)
 }
 
 // Storage order of the levels; the results do not change.  Level 0 is kept
-// in the mesh handle's internal order (when there are coarse levels), level
-// k in the order of each aggregate's first member in level k-1's storage
-// order (so the coarse levels inherit level 0's Morton locality), and the
-// coarsest level in its own order.  Rows, aggregates and their lists are
+// in the mesh handle's internal order (when there are coarse levels), the
+// middle levels in breadth-first order over their own graph, seeded in the
+// order of each aggregate's first member in the level above (bfs), or in
+// that inherited order itself, and the coarsest level in its own order.  Rows, aggregates and their lists are
 // moved, never reordered inside: a row keeps its entries in face order, an
 // aggregate its cells in ascending original order, so every sum is taken
 // in the same order.  Afterwards: rows (rptr, rcol, rfac, rlo) of levels >= 1
@@ -827,7 +827,7 @@ static void gamg_rows(GamgHostLevel& L)
 // cell numbers, which index the caller's diagonal, and ccell_int at internal
 // positions); faces (fptr, fface, l, u) keep their numbering.  perm0:
 // internal position -> original cell of level 0.
-static void gamg_store_order(std::vector<GamgHostLevel>& lv, const std::vector<int>& perm0)
+static void gamg_store_order(std::vector<GamgHostLevel>& lv, const std::vector<int>& perm0, bool bfs)
 {
     const int L = (int)lv.size();
     std::vector<std::vector<int>> pos(L), inv(L);
@@ -841,6 +841,37 @@ static void gamg_store_order(std::vector<GamgHostLevel>& lv, const std::vector<i
             for (int p = 0; p < n; p++) {
                 inv[0][p] = perm0[p];
                 pos[0][perm0[p]] = p;
+            }
+        } else if (bfs) {
+            // breadth-first from each unvisited cell in the inherited order:
+            // a cell's neighbours land within about one BFS front of it
+            std::vector<int> seed;
+            seed.reserve(n);
+            std::vector<char> seen(n, 0);
+            for (int q = 0; q < lv[k - 1].n; q++) {
+                const int c = lv[k - 1].agg[inv[k - 1][q]];
+                if (!seen[c]) {
+                    seen[c] = 1;
+                    seed.push_back(c);
+                }
+            }
+            const GamgHostLevel& H = lv[k];
+            int next = 0;
+            for (int c0 : seed) {
+                if (pos[k][c0] >= 0) continue;
+                int head = next;
+                pos[k][c0] = next;
+                inv[k][next++] = c0;
+                while (head < next) {
+                    const int c = inv[k][head++];
+                    for (int e = H.rptr[c]; e < H.rptr[c + 1]; e++) {
+                        const int d = H.rcol[e];
+                        if (pos[k][d] < 0) {
+                            pos[k][d] = next;
+                            inv[k][next++] = d;
+                        }
+                    }
+                }
             }
         } else {
             int next = 0;
@@ -1132,7 +1163,11 @@ spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_s
             return cuda_fail(e, "spuma_gamg_create: copy of the cell order");
         }
     }
-    gamg_store_order(G->lv, perm0);
+    // storage order of the middle levels: breadth-first (default) or
+    // inherited from the level above (SPUMA_GAMG_ORDER=inherited, a
+    // measurement override)
+    const char* ord = getenv("SPUMA_GAMG_ORDER");
+    gamg_store_order(G->lv, perm0, !(ord && std::string(ord) == "inherited"));
     G->bytes = gamg_layout(*G, false);
     G->small_from = (int)G->lv.size();
     for (int k = 0; k < (int)G->lv.size(); k++)

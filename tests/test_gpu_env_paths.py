@@ -1,7 +1,8 @@
 """The solvers' measurement overrides (SPUMA_SWEEP=0: DIC levels strided over
 the blocks; SPUMA_TAIL_ROWS=0: no small last levels on the first block;
 SPUMA_SOLVE_BLOCKS_PER_SM=1; SPUMA_GAMG_FUSE_SCALE_ROWS: GAMG's correction
-scaling inside the first smoothing sweep) change how a solve runs, never
+scaling inside the first smoothing sweep; SPUMA_GAMG_ORDER=inherited: GAMG's
+middle levels stored in the inherited order) change how a solve runs, never
 what it computes.  The library reads them once per process, so each setting
 runs in a child process (tests/env_path_child.py) that compares with the
 oracle: DIC factor and preconditioner bit for bit, FP64 PCG at matched
@@ -19,8 +20,10 @@ pytestmark = pytest.mark.gpu
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SETTINGS = [{}, {"SPUMA_SWEEP": "0"}, {"SPUMA_TAIL_ROWS": "0"}, {"SPUMA_SWEEP": "0", "SPUMA_TAIL_ROWS": "0"},
-            {"SPUMA_SOLVE_BLOCKS_PER_SM": "1"}, {"SPUMA_GAMG_FUSE_SCALE_ROWS": "1000000"}]
-IDS = ["default", "strided-levels", "no-tail", "strided-no-tail", "one-block-per-sm", "gamg-fused-scaling"]
+            {"SPUMA_SOLVE_BLOCKS_PER_SM": "1"}, {"SPUMA_GAMG_FUSE_SCALE_ROWS": "1000000"},
+            {"SPUMA_GAMG_ORDER": "inherited"}]
+IDS = ["default", "strided-levels", "no-tail", "strided-no-tail", "one-block-per-sm", "gamg-fused-scaling",
+       "gamg-inherited-order"]
 
 
 @pytest.mark.parametrize("env", SETTINGS, ids=IDS)
