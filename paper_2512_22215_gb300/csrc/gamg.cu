@@ -28,7 +28,9 @@
 // per-row sum follows the sequential definition's order; dot products are
 // deterministic block/grid reductions.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <string>
 #include <vector>
 
@@ -1077,12 +1079,23 @@ spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_s
         delete G;
         return cuda_fail(e, "spuma_gamg_create: copy of the addressing");
     }
+    // host-time breakdown of the build (SPUMA_GAMG_TIMING: printed to stderr)
+    double t_rows = 0, t_agg = 0, t_faces = 0, t_lists = 0, t_order = 0;
+    auto now = [] { return std::chrono::steady_clock::now(); };
+    auto secs = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+        return std::chrono::duration<double>(b - a).count();
+    };
+    auto tp = now();
     G->lv.push_back(std::move(L0));
     gamg_rows(G->lv[0]);
+    t_rows += secs(tp, now());
     while ((int)G->lv.size() < kGamgMaxLevels && G->lv.back().n > kGamgCoarsest) {
         GamgHostLevel& F = G->lv.back();
+        tp = now();
         const int nc = gamg_agglomerate(F, w, F.agg);
+        t_agg += secs(tp, now());
         if (nc >= F.n) break;
+        tp = now();
         // coarse faces: (min, max) aggregate pairs, sorted, fine faces in
         // ascending order within each pair: two stable counting-sort passes
         // (by max, then by min) over the faces in face order, O(F + nc)
@@ -1134,6 +1147,8 @@ spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_s
         }
         F.fptr.push_back((int)m);
         C.nf = (int)C.l.size();
+        t_faces += secs(tp, now());
+        tp = now();
         // next-level cell -> cells, -> faces inside it (ascending)
         F.cptr.assign(nc + 1, 0);
         for (int i = 0; i < F.n; i++) F.cptr[F.agg[i] + 1]++;
@@ -1149,7 +1164,10 @@ spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_s
         cur.assign(F.iptr.begin(), F.iptr.end() - 1);
         for (int f = 0; f < F.nf; f++)
             if (F.agg[F.l[f]] == F.agg[F.u[f]]) F.iface[cur[F.agg[F.l[f]]]++] = f;
+        t_lists += secs(tp, now());
+        tp = now();
         gamg_rows(C);
+        t_rows += secs(tp, now());
         G->lv.push_back(std::move(C));
         w.swap(wc);
     }
@@ -1167,7 +1185,12 @@ spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_s
     // inherited from the level above (SPUMA_GAMG_ORDER=inherited, a
     // measurement override)
     const char* ord = getenv("SPUMA_GAMG_ORDER");
+    tp = now();
     gamg_store_order(G->lv, perm0, !(ord && std::string(ord) == "inherited"));
+    t_order += secs(tp, now());
+    if (getenv("SPUMA_GAMG_TIMING"))
+        fprintf(stderr, "spuma_gamg_create host seconds: rows %.3f agglomerate %.3f coarse faces %.3f lists %.3f "
+                "storage order %.3f\n", t_rows, t_agg, t_faces, t_lists, t_order);
     G->bytes = gamg_layout(*G, false);
     G->small_from = (int)G->lv.size();
     for (int k = 0; k < (int)G->lv.size(); k++)
