@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 SOURCES = ["topology.cu", "solve.cu", "ops.cu", "fvops.cu", "gamg.cu", "batch.cu", "noalloc.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-         "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-Xptxas", "-v"]
+         "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "--expt-relaxed-constexpr", "-Xptxas", "-v"]
 
 
 def _deps():
@@ -42,7 +42,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, log in results:
             sys.stderr.write(log)
     tmp = OUT + f".tmp{os.getpid()}"
-    subprocess.check_call([NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp,
+    subprocess.check_call([NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-Xcompiler", "-pthread",
+                           "-o", tmp,
                            *[o for o, _ in results]])
     os.replace(tmp, OUT)
     with open(os.path.join(BUILD, "ptxas.log"), "w") as fh:

@@ -32,6 +32,7 @@
 #include <cmath>
 #include <cstdio>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -815,6 +816,74 @@ static void gamg_rows(GamgHostLevel& L)
     }
 }
 
+// f(begin, end) over [0, n) in contiguous pieces on the host's cores (loops
+// whose iterations write disjoint entries).
+template <class Fn>
+static void par_for(size_t n, Fn f, size_t min_n = 65536)
+{
+    const unsigned hc = std::thread::hardware_concurrency();
+    const size_t T = std::min<size_t>(16, hc > 0 ? hc : 1);
+    if (n < min_n || T == 1) {
+        f((size_t)0, n);
+        return;
+    }
+    const size_t chunk = (n + T - 1) / T;
+    std::vector<std::thread> th;
+    for (size_t t = 0; t < T; t++) {
+        const size_t a = t * chunk, b = std::min(n, a + chunk);
+        if (a < b) th.emplace_back(f, a, b);
+    }
+    for (auto& x : th) x.join();
+}
+
+// Stable least-significant-digit radix sort of (key, val) by key below kmax,
+// 11-bit digits, each pass split over the host's cores (per-piece digit
+// counts, so the scatter keeps every piece's order and the pieces' order).
+static void radix_sort_stable(std::vector<uint64_t>& key, std::vector<int>& val, uint64_t kmax)
+{
+    const size_t m = key.size();
+    const unsigned hc = std::thread::hardware_concurrency();
+    const size_t T = m < 65536 ? 1 : std::min<size_t>(16, hc > 0 ? hc : 1);
+    const size_t chunk = (m + T - 1) / T;
+    std::vector<uint64_t> key2(m);
+    std::vector<int> val2(m);
+    std::vector<size_t> cnt(T * 2048);
+    for (int shift = 0; shift < 64 && (kmax >> shift) > 0; shift += 11) {
+        std::fill(cnt.begin(), cnt.end(), 0);
+        auto count = [&](size_t t) {
+            const size_t a = t * chunk, b = std::min(m, a + chunk);
+            size_t* c = cnt.data() + t * 2048;
+            for (size_t j = a; j < b; j++) c[(key[j] >> shift) & 2047u]++;
+        };
+        auto scatter = [&](size_t t) {
+            const size_t a = t * chunk, b = std::min(m, a + chunk);
+            size_t* c = cnt.data() + t * 2048;
+            for (size_t j = a; j < b; j++) {
+                const size_t o = c[(key[j] >> shift) & 2047u]++;
+                key2[o] = key[j];
+                val2[o] = val[j];
+            }
+        };
+        auto run = [&](auto fn) {
+            std::vector<std::thread> th;
+            for (size_t t = 1; t < T; t++) th.emplace_back(fn, t);
+            fn((size_t)0);
+            for (auto& x : th) x.join();
+        };
+        run(count);
+        size_t base = 0;   // digit-major, piece-minor exclusive prefix
+        for (int d = 0; d < 2048; d++)
+            for (size_t t = 0; t < T; t++) {
+                const size_t c = cnt[t * 2048 + d];
+                cnt[t * 2048 + d] = base;
+                base += c;
+            }
+        run(scatter);
+        key.swap(key2);
+        val.swap(val2);
+    }
+}
+
 // Storage order of the levels; the results do not change.  Level 0 is kept
 // in the mesh handle's internal order (when there are coarse levels), the
 // middle levels in breadth-first order over their own graph, seeded in the
@@ -889,41 +958,56 @@ static void gamg_store_order(std::vector<GamgHostLevel>& lv, const std::vector<i
     for (int k = 0; k < L; k++) {
         GamgHostLevel& H = lv[k];
         // rows: lower entries (column below the row in the original order)
-        // lead each row, faces being sorted by (lower, upper)
-        std::vector<int> rptr(H.n + 1, 0), rcol, rfac, rlo(H.n, 0);
-        rcol.reserve(H.rcol.size());
-        rfac.reserve(H.rfac.size());
+        // lead each row, faces being sorted by (lower, upper); level 0's rows
+        // stay in original order
+        std::vector<int> rptr(H.n + 1, 0), rcol(H.rcol.size()), rfac(H.rfac.size()), rlo(H.n, 0);
+        const int* I = k == 0 ? nullptr : inv[k].data();
+        const int* P = k == 0 ? nullptr : pos[k].data();
         for (int q = 0; q < H.n; q++) {
-            const int c = k == 0 ? q : inv[k][q];   // level 0's rows stay in original order
-            const int* P = k == 0 ? nullptr : pos[k].data();
-            for (int e = H.rptr[c]; e < H.rptr[c + 1]; e++) {
-                rcol.push_back(P ? P[H.rcol[e]] : H.rcol[e]);
-                rfac.push_back(H.rfac[e]);
-                if (H.rcol[e] < c) rlo[q]++;
-            }
-            rptr[q + 1] = (int)rcol.size();
+            const int c = I ? I[q] : q;
+            rptr[q + 1] = rptr[q] + (H.rptr[c + 1] - H.rptr[c]);
         }
+        par_for((size_t)H.n, [&](size_t q0, size_t q1) {
+            for (size_t q = q0; q < q1; q++) {
+                const int c = I ? I[q] : (int)q;
+                int o = rptr[q], lo = 0;
+                for (int e = H.rptr[c]; e < H.rptr[c + 1]; e++, o++) {
+                    rcol[o] = P ? P[H.rcol[e]] : H.rcol[e];
+                    rfac[o] = H.rfac[e];
+                    if (H.rcol[e] < c) lo++;
+                }
+                rlo[q] = lo;
+            }
+        });
         H.rptr.swap(rptr);
         H.rcol.swap(rcol);
         H.rfac.swap(rfac);
         H.rlo.swap(rlo);
         if (k + 1 >= L) continue;
         const int nc = lv[k + 1].n;
-        std::vector<int> agg(H.n), cptr(nc + 1, 0), ccell, iptr(nc + 1, 0), iface, ccell_int;
-        for (int q = 0; q < H.n; q++) agg[q] = pos[k + 1][H.agg[inv[k][q]]];
-        ccell.reserve(H.ccell.size());
-        iface.reserve(H.iface.size());
+        std::vector<int> agg(H.n), cptr(nc + 1, 0), ccell(H.ccell.size()), iptr(nc + 1, 0), iface(H.iface.size()),
+            ccell_int(k == 0 ? H.ccell.size() : 0);
+        par_for((size_t)H.n, [&](size_t q0, size_t q1) {
+            for (size_t q = q0; q < q1; q++) agg[q] = pos[k + 1][H.agg[inv[k][q]]];
+        });
         for (int qc = 0; qc < nc; qc++) {
             const int c = inv[k + 1][qc];
-            for (int j = H.cptr[c]; j < H.cptr[c + 1]; j++) {
-                const int fine = H.ccell[j];
-                ccell.push_back(k == 0 ? fine : pos[k][fine]);
-                if (k == 0) ccell_int.push_back(pos[0][fine]);
-            }
-            for (int j = H.iptr[c]; j < H.iptr[c + 1]; j++) iface.push_back(H.iface[j]);
-            cptr[qc + 1] = (int)ccell.size();
-            iptr[qc + 1] = (int)iface.size();
+            cptr[qc + 1] = cptr[qc] + (H.cptr[c + 1] - H.cptr[c]);
+            iptr[qc + 1] = iptr[qc] + (H.iptr[c + 1] - H.iptr[c]);
         }
+        par_for((size_t)nc, [&](size_t q0, size_t q1) {
+            for (size_t qc = q0; qc < q1; qc++) {
+                const int c = inv[k + 1][qc];
+                int o = cptr[qc];
+                for (int j = H.cptr[c]; j < H.cptr[c + 1]; j++, o++) {
+                    const int fine = H.ccell[j];
+                    ccell[o] = k == 0 ? fine : pos[k][fine];
+                    if (k == 0) ccell_int[o] = pos[0][fine];
+                }
+                o = iptr[qc];
+                for (int j = H.iptr[c]; j < H.iptr[c + 1]; j++, o++) iface[o] = H.iface[j];
+            }
+        });
         H.agg.swap(agg);
         H.cptr.swap(cptr);
         H.ccell.swap(ccell);
@@ -1066,11 +1150,20 @@ spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_s
     L0.l.resize(h->nf);
     L0.u.resize(h->nf);
     std::vector<double> w(h->nf);
+    // the mesh handle's per-cell face lists (original order): neighbour-side
+    // faces ascending with their lower cells, owner-side faces as a range
+    std::vector<int> own_start(h->n + 1), lo_start(h->n + 1), lo_face(h->nf), lo_col(h->nf);
     cudaError_t e = cudaSuccess;
     if (h->nf > 0) {
-        e = cudaMemcpyAsync(L0.l.data(), h->at<int>(h->L.laddr), 4 * (size_t)h->nf, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(L0.u.data(), h->at<int>(h->L.uaddr), 4 * (size_t)h->nf, cudaMemcpyDeviceToHost, s);
+        auto get = [&](void* dst, size_t off, size_t bytes) {
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dst, h->at<char>(off), bytes, cudaMemcpyDeviceToHost, s);
+        };
+        get(L0.l.data(), h->L.laddr, 4 * (size_t)h->nf);
+        get(L0.u.data(), h->L.uaddr, 4 * (size_t)h->nf);
+        get(own_start.data(), h->L.own_start, 4 * ((size_t)h->n + 1));
+        get(lo_start.data(), h->L.lo_start, 4 * ((size_t)h->n + 1));
+        get(lo_face.data(), h->L.lo_face, 4 * (size_t)h->nf);
+        get(lo_col.data(), h->L.lo_col, 4 * (size_t)h->nf);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(w.data(), face_weight, 8 * (size_t)h->nf, cudaMemcpyDeviceToHost, s);
     }
@@ -1087,7 +1180,31 @@ spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_s
     };
     auto tp = now();
     G->lv.push_back(std::move(L0));
-    gamg_rows(G->lv[0]);
+    if (h->nf > 0) {
+        // level 0's rows from those lists: the same entries, in face order, as
+        // gamg_rows builds (lower entries first, faces being sorted by owner)
+        GamgHostLevel& H = G->lv[0];
+        H.rptr.assign(H.n + 1, 0);
+        for (int i = 0; i < H.n; i++)
+            H.rptr[i + 1] = H.rptr[i] + (lo_start[i + 1] - lo_start[i]) + (own_start[i + 1] - own_start[i]);
+        H.rcol.resize(2 * (size_t)H.nf);
+        H.rfac.resize(2 * (size_t)H.nf);
+        par_for((size_t)H.n, [&](size_t i0, size_t i1) {
+            for (size_t i = i0; i < i1; i++) {
+                int o = H.rptr[i];
+                for (int k = lo_start[i]; k < lo_start[i + 1]; k++, o++) {
+                    H.rcol[o] = lo_col[k];
+                    H.rfac[o] = lo_face[k];
+                }
+                for (int f = own_start[i]; f < own_start[i + 1]; f++, o++) {
+                    H.rcol[o] = H.u[f];
+                    H.rfac[o] = f;
+                }
+            }
+        });
+    } else {
+        gamg_rows(G->lv[0]);
+    }
     t_rows += secs(tp, now());
     while ((int)G->lv.size() < kGamgMaxLevels && G->lv.back().n > kGamgCoarsest) {
         GamgHostLevel& F = G->lv.back();
@@ -1097,55 +1214,67 @@ spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_s
         if (nc >= F.n) break;
         tp = now();
         // coarse faces: (min, max) aggregate pairs, sorted, fine faces in
-        // ascending order within each pair: two stable counting-sort passes
-        // (by max, then by min) over the faces in face order, O(F + nc)
-        std::vector<int> fa, fb, ord, tmp;
-        fa.reserve(F.nf);
-        fb.reserve(F.nf);
-        for (int f = 0; f < F.nf; f++) {
-            const int a = F.agg[F.l[f]], b = F.agg[F.u[f]];
-            if (a != b) {
-                fa.push_back(std::min(a, b));
-                fb.push_back(std::max(a, b));
-                ord.push_back(f);
-            }
+        // ascending order within each pair: a stable least-significant-digit
+        // radix sort (11-bit digits) of the keys min * nc + max, taken in face
+        // order (each pass streams through 2048 buckets: no random access over
+        // the whole array, unlike a counting sort on the cell numbers)
+        std::vector<uint64_t> key;
+        std::vector<int> ord;
+        {
+            // the faces between different aggregates, in face order: counted
+            // per piece of the face range, then written at the pieces' offsets
+            const size_t P = 64, piece = ((size_t)F.nf + P - 1) / P;
+            std::vector<size_t> off(P + 1, 0);
+            par_for(P, [&](size_t p0, size_t p1) {
+                for (size_t p = p0; p < p1; p++) {
+                    size_t c = 0;
+                    for (size_t f = p * piece; f < std::min((size_t)F.nf, (p + 1) * piece); f++)
+                        c += F.agg[F.l[f]] != F.agg[F.u[f]];
+                    off[p + 1] = c;
+                }
+            }, F.nf >= 65536 ? 1 : P + 1);
+            for (size_t p = 0; p < P; p++) off[p + 1] += off[p];
+            key.resize(off[P]);
+            ord.resize(off[P]);
+            par_for(P, [&](size_t p0, size_t p1) {
+                for (size_t p = p0; p < p1; p++) {
+                    size_t o = off[p];
+                    for (size_t f = p * piece; f < std::min((size_t)F.nf, (p + 1) * piece); f++) {
+                        const int a = F.agg[F.l[f]], b = F.agg[F.u[f]];
+                        if (a != b) {
+                            key[o] = (uint64_t)std::min(a, b) * (uint64_t)nc + (uint64_t)std::max(a, b);
+                            ord[o++] = (int)f;
+                        }
+                    }
+                }
+            }, F.nf >= 65536 ? 1 : P + 1);
         }
         const size_t m = ord.size();
-        {
-            std::vector<int> pos(nc + 1, 0);
-            std::vector<int> key(m);
-            tmp.resize(m);
-            for (int pass = 0; pass < 2; pass++) {   // pass 0: by max (fb), pass 1: by min (fa)
-                const std::vector<int>& k = pass == 0 ? fb : fa;
-                std::fill(pos.begin(), pos.end(), 0);
-                for (size_t j = 0; j < m; j++) {
-                    key[j] = k[pass == 0 ? j : (size_t)tmp[j]];
-                    pos[key[j] + 1]++;
-                }
-                for (int c = 0; c < nc; c++) pos[c + 1] += pos[c];
-                std::vector<int> out(m);
-                for (size_t j = 0; j < m; j++) out[pos[key[j]]++] = pass == 0 ? (int)j : tmp[j];
-                tmp.swap(out);
-            }
-        }
-        // tmp: indices into (fa, fb, ord) sorted by (min, max), ties in face order
+        radix_sort_stable(key, ord, (uint64_t)nc * (uint64_t)nc);
+        // (key, ord) sorted by (min, max), ties in face order
+        // runs of equal keys are the coarse faces; each one's weight is the
+        // sum of its fine faces' weights in face order (runs in parallel)
         GamgHostLevel C;
         C.n = nc;
-        F.fptr.assign(1, 0);
-        F.fface.reserve(m);
-        std::vector<double> wc;
-        for (size_t j = 0; j < m; j++) {
-            const int t = tmp[j];
-            if (j == 0 || fa[t] != fa[tmp[j - 1]] || fb[t] != fb[tmp[j - 1]]) {
-                if (j > 0) F.fptr.push_back((int)j);
-                C.l.push_back(fa[t]);
-                C.u.push_back(fb[t]);
-                wc.push_back(0.0);
-            }
-            wc.back() += w[ord[t]];
-            F.fface.push_back(ord[t]);
-        }
+        F.fptr.clear();
+        for (size_t j = 0; j < m; j++)
+            if (j == 0 || key[j] != key[j - 1]) F.fptr.push_back((int)j);
         F.fptr.push_back((int)m);
+        const size_t ncf = F.fptr.size() - 1;
+        C.l.resize(ncf);
+        C.u.resize(ncf);
+        std::vector<double> wc(ncf);
+        par_for(ncf, [&](size_t g0, size_t g1) {
+            for (size_t g = g0; g < g1; g++) {
+                const uint64_t kk = key[F.fptr[g]];
+                C.l[g] = (int)(kk / (uint64_t)nc);
+                C.u[g] = (int)(kk % (uint64_t)nc);
+                double sum = 0.0;
+                for (int j = F.fptr[g]; j < F.fptr[g + 1]; j++) sum += w[ord[j]];
+                wc[g] = sum;
+            }
+        });
+        F.fface.swap(ord);
         C.nf = (int)C.l.size();
         t_faces += secs(tp, now());
         tp = now();

@@ -119,3 +119,26 @@ def test_gamg_then_prepared_matrix_calls(gc):
     assert np.array_equal(M.precondition(r, 2).cpu().numpy(), w0)
     x1, p1 = M.solve(dev(dg), dev(up), dev(c.b), None, SolverControls(precond=2, tolerance=1e-10))
     assert p1["n_iter"] == p0["n_iter"] and np.array_equal(x1.cpu().numpy(), x0.cpu().numpy())
+
+
+@pytest.mark.slow
+def test_large_mesh_hierarchy_and_vcycles():
+    """A mesh large enough (110,592 cells, 324,864 faces) for the hierarchy
+    build's multi-threaded passes (face keys, radix sort, row and list
+    copies): the same level sizes as the oracle, and x after 10 V-cycles of
+    each smoother at 1e-8 of the oracle's."""
+    from paper_2512_22215_gb300 import GamgSolver, SolverControls
+    c = hexmesh.pressure_case(48, seed=107, jitter=0.2, permute=True, lognormal_gamma=True)
+    m = c.mesh
+    assert m.n_cells >= 65536 and m.n_faces >= 65536
+    M = mesh_of(c, centres=True)
+    up, dg = oracle.assemble_laplacian(m, c.gamma, c.bgamma, c.btype)
+    w = np.abs(up)
+    levels = G.hierarchy(m.n_cells, m.lower, m.upper_addr, w)
+    for smoother, name in ((0, "richardson"), (1, "gs2")):
+        S = GamgSolver(M, dev(w), smoother=smoother)
+        assert S.level_cells == [lv["n"] for lv in levels]
+        x, p = S.solve(dev(dg), dev(up), dev(c.b), None, SolverControls(tolerance=0.0, max_iter=10))
+        assert p["n_iter"] == 10 and p["status"] == 0
+        xo, _, _ = G.gamg(m.lower, m.upper_addr, dg, up, c.b, w, tol=0.0, max_iter=10, smoother=name)
+        assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-8 * np.linalg.norm(xo)
