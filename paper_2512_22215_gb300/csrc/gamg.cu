@@ -24,9 +24,12 @@
 // optimal step (e.r)/(e.Ae); two damped-Jacobi sweeps e += (2/3 rD)(r - Ae)
 // (or two two-stage Gauss-Seidel sweeps e += (D^-1 - D^-1 L D^-1)(r - A e)).
 // Levels of at most two rows per thread of one block run on the first block
-// alone with block-level barriers; the others on the whole grid.  Every
-// per-row sum follows the sequential definition's order; dot products are
-// deterministic block/grid reductions.
+// alone with block-level barriers (the coarsest level's PCG on one warp when
+// it has at most 32 cells); the others on the whole grid.  Storage: level 0
+// in the mesh handle's internal (DIC level, Morton) order, the middle levels
+// breadth-first, the coarsest as built; rows and aggregates are moved, never
+// reordered inside, so every per-row sum follows the sequential definition's
+// order; dot products are deterministic block/grid reductions.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
