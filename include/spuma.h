@@ -51,7 +51,8 @@ typedef enum {
     SPUMA_ERR_SINGULAR = 5,              /* |p.Ap| / normFactor < 1e-300               */
     SPUMA_ERR_NOT_SPD = 6,               /* a DIC pivot is <= 0                         */
     SPUMA_ERR_NONFINITE = 7,             /* NaN or Inf among the coefficients or b      */
-    SPUMA_ERR_DEVICE_TIMEOUT = 8         /* a grid barrier waited past its time limit   */
+    SPUMA_ERR_DEVICE_TIMEOUT = 8,        /* a grid barrier waited past its time limit   */
+    SPUMA_ERR_HOST = 9                   /* a host allocation or thread failed          */
 } spuma_status;
 
 typedef enum { SPUMA_F64 = 0, SPUMA_MIXED = 1, SPUMA_F32 = 2, SPUMA_MIXED_RESTART = 3 } spuma_precision;
@@ -375,8 +376,11 @@ spuma_status spuma_pbicg_solve(spuma_ldu_t h, const double* diag, const double* 
  *   neighbours are taken; no faces: stay alone); coarse faces between
  *   different aggregates, sorted by (min, max), weights summed; levels added
  *   while the coarse level has more than 10 cells and fewer than the level
- *   above.  spuma_gamg_workspace_bytes then gives the device workspace that
- *   spuma_gamg_bind takes (256-byte aligned; synchronous upload).
+ *   above.  The independent passes of the build run on the host's cores
+ *   (the agglomeration itself is sequential); a host allocation or thread
+ *   failure returns SPUMA_ERR_HOST.  spuma_gamg_workspace_bytes then gives
+ *   the device workspace that spuma_gamg_bind takes (256-byte aligned;
+ *   synchronous upload).
  * spuma_gamg_solve: one persistent cooperative launch: Galerkin coarse
  *   matrices P^T A P (P piecewise constant; sums in ascending fine order:
  *   upper_F = sum of the fine upper_f of F; diag_C = sum of the fine diag of

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libspuma.so")
 
 SPUMA_OK = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_UPPER_TRIANGULAR", 3: "CUDA", 4: "WORKSPACE_TOO_SMALL",
-                5: "SINGULAR", 6: "NOT_SPD", 7: "NONFINITE", 8: "DEVICE_TIMEOUT"}
+                5: "SINGULAR", 6: "NOT_SPD", 7: "NONFINITE", 8: "DEVICE_TIMEOUT", 9: "HOST"}
 F64, MIXED, F32, MIXED_RESTART = 0, 1, 2, 3
 PRECOND_NONE, PRECOND_DIAGONAL, PRECOND_DIC, PRECOND_DILU = 0, 1, 2, 3
 WORKSPACE_ASYMMETRIC = 1

@@ -34,6 +34,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <memory>
+#include <stdexcept>
+#include <system_error>
 #include <string>
 #include <thread>
 #include <vector>
@@ -832,9 +835,15 @@ static void par_for(size_t n, Fn f, size_t min_n = 65536)
     }
     const size_t chunk = (n + T - 1) / T;
     std::vector<std::thread> th;
+    th.reserve(T);
     for (size_t t = 0; t < T; t++) {
         const size_t a = t * chunk, b = std::min(n, a + chunk);
-        if (a < b) th.emplace_back(f, a, b);
+        if (a >= b) continue;
+        try {
+            th.emplace_back(f, a, b);
+        } catch (const std::system_error&) {
+            f(a, b);   // no thread to be had: this piece on the calling thread
+        }
     }
     for (auto& x : th) x.join();
 }
@@ -869,7 +878,14 @@ static void radix_sort_stable(std::vector<uint64_t>& key, std::vector<int>& val,
         };
         auto run = [&](auto fn) {
             std::vector<std::thread> th;
-            for (size_t t = 1; t < T; t++) th.emplace_back(fn, t);
+            th.reserve(T);
+            for (size_t t = 1; t < T; t++) {
+                try {
+                    th.emplace_back(fn, t);
+                } catch (const std::system_error&) {
+                    fn(t);   // no thread to be had: this piece on the calling thread
+                }
+            }
             fn((size_t)0);
             for (auto& x : th) x.join();
         };
@@ -1136,7 +1152,7 @@ size_t gamg_layout(spuma_gamg& G, bool assign)
 
 extern "C" {
 
-spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_stream_t stream, spuma_gamg_t* out)
+static spuma_status gamg_create(spuma_ldu_t h, const double* face_weight, spuma_stream_t stream, spuma_gamg_t* out)
 {
     if (!out) { set_error("out is NULL"); return SPUMA_ERR_INVALID_ARG; }
     *out = nullptr;
@@ -1145,7 +1161,7 @@ spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_s
         return SPUMA_ERR_INVALID_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    spuma_gamg* G = new spuma_gamg();
+    std::unique_ptr<spuma_gamg> G(new spuma_gamg());
     G->h = h;
     GamgHostLevel L0;
     L0.n = h->n;
@@ -1172,7 +1188,6 @@ spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_s
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
-        delete G;
         return cuda_fail(e, "spuma_gamg_create: copy of the addressing");
     }
     // host-time breakdown of the build (SPUMA_GAMG_TIMING: printed to stderr)
@@ -1309,8 +1324,7 @@ spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_s
         e = cudaMemcpyAsync(perm0.data(), h->at<int>(h->L.perm), 4 * (size_t)h->n, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
-            delete G;
-            return cuda_fail(e, "spuma_gamg_create: copy of the cell order");
+                return cuda_fail(e, "spuma_gamg_create: copy of the cell order");
         }
     }
     // storage order of the middle levels: breadth-first (default) or
@@ -1330,8 +1344,20 @@ spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_s
             G->small_from = k;
             break;
         }
-    *out = G;
+    *out = G.release();
     return SPUMA_OK;
+}
+
+// No C++ exception crosses the C interface: a host allocation or thread
+// that fails while the hierarchy is built returns SPUMA_ERR_HOST.
+spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_stream_t stream, spuma_gamg_t* out)
+{
+    try {
+        return gamg_create(h, face_weight, stream, out);
+    } catch (const std::exception& e) {
+        set_error(std::string("spuma_gamg_create: host failure: ") + e.what());
+        return SPUMA_ERR_HOST;
+    }
 }
 
 size_t spuma_gamg_workspace_bytes(spuma_gamg_t g) { return g ? g->bytes : 0; }

@@ -533,6 +533,7 @@ const char* spuma_status_string(int32_t s)
     case SPUMA_ERR_NOT_SPD: return "matrix not SPD (non-positive DIC pivot)";
     case SPUMA_ERR_NONFINITE: return "non-finite input";
     case SPUMA_ERR_DEVICE_TIMEOUT: return "device grid barrier timed out";
+    case SPUMA_ERR_HOST: return "host allocation or thread failed";
     default: return "unknown status";
     }
 }

@@ -44,8 +44,9 @@ def test_exports_every_declared_symbol(L):
 
 
 def test_status_strings(L):
-    for s in range(9):
+    for s in range(10):
         assert len(L.spuma_status_string(s)) >= 2
+    assert L.spuma_status_string(9) != b"unknown status"
     assert L.spuma_status_string(99) == b"unknown status"
 
 
