@@ -211,12 +211,10 @@ static std::string batch_signature(const spuma_batch* bt, const spuma_solver_con
     return buf;
 }
 
-extern "C" {
-
-spuma_status spuma_batch_create(int32_t n_sys, const spuma_ldu_t* hs, const double* const* diag,
-                                const double* const* upper, const double* const* b, double* const* x,
-                                const spuma_solver_controls* ctl, spuma_solver_perf* perf, int32_t flags,
-                                spuma_stream_t stream, spuma_batch_t* out)
+static spuma_status batch_create(int32_t n_sys, const spuma_ldu_t* hs, const double* const* diag,
+                                 const double* const* upper, const double* const* b, double* const* x,
+                                 const spuma_solver_controls* ctl, spuma_solver_perf* perf, int32_t flags,
+                                 spuma_stream_t stream, spuma_batch_t* out)
 {
     if (!out) { set_error("out is NULL"); return SPUMA_ERR_INVALID_ARG; }
     *out = nullptr;
@@ -378,6 +376,17 @@ spuma_status spuma_batch_create(int32_t n_sys, const spuma_ldu_t* hs, const doub
     return SPUMA_OK;
 }
 
+extern "C" {
+
+spuma_status spuma_batch_create(int32_t n_sys, const spuma_ldu_t* hs, const double* const* diag,
+                                const double* const* upper, const double* const* b, double* const* x,
+                                const spuma_solver_controls* ctl, spuma_solver_perf* perf, int32_t flags,
+                                spuma_stream_t stream, spuma_batch_t* out)
+{
+    return host_guard("spuma_batch_create",
+                      [&] { return batch_create(n_sys, hs, diag, upper, b, x, ctl, perf, flags, stream, out); });
+}
+
 spuma_status spuma_batch_run(spuma_batch_t bt, spuma_stream_t stream)
 {
     if (!bt) { set_error("batch is NULL"); return SPUMA_ERR_INVALID_ARG; }
@@ -447,19 +456,27 @@ int32_t spuma_tune_cache_lookup(const char* path, const char* signature, int32_t
                                 int32_t* grid_div, double* ms)
 {
     if (!signature || !threads || !policy || !grid_div || !ms) return 0;
-    int t, p, d;
-    if (!tune_cache_lookup(path, signature, &t, &p, &d, ms)) return 0;
-    *threads = t;
-    *policy = p;
-    *grid_div = d;
-    return 1;
+    try {
+        int t, p, d;
+        if (!tune_cache_lookup(path, signature, &t, &p, &d, ms)) return 0;
+        *threads = t;
+        *policy = p;
+        *grid_div = d;
+        return 1;
+    } catch (...) {
+        return 0;   // a host failure reads as a cache miss
+    }
 }
 
 int32_t spuma_tune_cache_store(const char* path, const char* signature, int32_t threads, int32_t policy,
                                int32_t grid_div, double ms)
 {
     if (!signature || grid_div < 1) return 0;
-    return tune_cache_store(path, signature, threads, policy, grid_div, ms) ? 1 : 0;
+    try {
+        return tune_cache_store(path, signature, threads, policy, grid_div, ms) ? 1 : 0;
+    } catch (...) {
+        return 0;
+    }
 }
 
 }  // extern "C"

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <exception>
 #include <string>
 #include <vector>
 
@@ -20,6 +21,21 @@ constexpr int kWarp = 32;
 // ---------------------------------------------------------------- errors --
 void set_error(const std::string& msg);
 spuma_status cuda_fail(cudaError_t e, const char* what);
+
+// An entry point's body run so that no C++ exception crosses the C
+// interface: a failed host allocation or thread returns SPUMA_ERR_HOST.
+template <class F>
+inline spuma_status host_guard(const char* where, F f)
+{
+    try {
+        return f();
+    } catch (const std::exception& e) {
+        set_error(std::string(where) + ": host failure: " + e.what());
+    } catch (...) {
+        set_error(std::string(where) + ": host failure");
+    }
+    return SPUMA_ERR_HOST;
+}
 void count_launch(uint64_t n = 1);
 uint64_t barrier_timeout_ns();
 

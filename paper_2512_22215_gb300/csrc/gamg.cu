@@ -1352,12 +1352,7 @@ static spuma_status gamg_create(spuma_ldu_t h, const double* face_weight, spuma_
 // that fails while the hierarchy is built returns SPUMA_ERR_HOST.
 spuma_status spuma_gamg_create(spuma_ldu_t h, const double* face_weight, spuma_stream_t stream, spuma_gamg_t* out)
 {
-    try {
-        return gamg_create(h, face_weight, stream, out);
-    } catch (const std::exception& e) {
-        set_error(std::string("spuma_gamg_create: host failure: ") + e.what());
-        return SPUMA_ERR_HOST;
-    }
+    return host_guard("spuma_gamg_create", [&] { return gamg_create(h, face_weight, stream, out); });
 }
 
 size_t spuma_gamg_workspace_bytes(spuma_gamg_t g) { return g ? g->bytes : 0; }

@@ -554,9 +554,19 @@ spuma_status spuma_ldu_create(int32_t n, int32_t nf, const int32_t* l, const int
     return spuma_ldu_create_with_centres(n, nf, l, u, nullptr, workspace, workspace_bytes, stream, out);
 }
 
+static spuma_status ldu_create(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, const double* cell_c,
+                               void* workspace, size_t workspace_bytes, spuma_stream_t stream, spuma_ldu_t* out);
+
 spuma_status spuma_ldu_create_with_centres(int32_t n, int32_t nf, const int32_t* l, const int32_t* u,
                                            const double* cell_c, void* workspace, size_t workspace_bytes,
                                            spuma_stream_t stream, spuma_ldu_t* out)
+{
+    return host_guard("spuma_ldu_create",
+                      [&] { return ldu_create(n, nf, l, u, cell_c, workspace, workspace_bytes, stream, out); });
+}
+
+static spuma_status ldu_create(int32_t n, int32_t nf, const int32_t* l, const int32_t* u, const double* cell_c,
+                               void* workspace, size_t workspace_bytes, spuma_stream_t stream, spuma_ldu_t* out)
 {
     if (!out) { set_error("out is NULL"); return SPUMA_ERR_INVALID_ARG; }
     *out = nullptr;
