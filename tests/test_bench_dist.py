@@ -71,3 +71,23 @@ def test_cpulist_parsing():
     assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
     assert bench.parse_cpulist("5") == {5}
     assert bench.parse_cpulist("") == set()
+
+
+def test_traffic_record_scaling(monkeypatch):
+    """The roofline traffic record scales from the captured case by the
+    algorithmic bytes, and is withheld once the solver source has changed."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    with open(os.path.join(ROOT, "paper_2512_22215_gb300", "csrc", "solve.cu"), "rb") as fh:
+        sha = hashlib.sha1(fh.read()).hexdigest()
+    rec = {"solve_cu_sha1": sha, "n": 128, "bytes": 10 ** 11, "inner": 500, "outer": 4}
+    monkeypatch.setattr(bench, "TRAFFIC", rec)
+    n, nf = 128 ** 3, 3 * 127 * 128 * 128
+    assert bench.traffic_bytes(n, nf, 500, 4) == 10 ** 11                      # the captured case itself
+    w = bench.workload_bytes(8_000_000, 23_880_000)
+    wc = bench.workload_bytes(n, nf)
+    want = 10 ** 11 * (795 * w["it32"] + 5 * w["resid64"]) / (500 * wc["it32"] + 5 * wc["resid64"])
+    assert abs(bench.traffic_bytes(8_000_000, 23_880_000, 795, 4) - want) <= 1
+    monkeypatch.setattr(bench, "TRAFFIC", dict(rec, solve_cu_sha1="0" * 40))
+    assert bench.traffic_bytes(n, nf, 500, 4) is None
